@@ -1,0 +1,354 @@
+"""Benchmark: MLUPS/species of the fused LBM / Maxwell-Stefan step on GB300.
+
+Default workload: the 3-D D3Q19 ternary anode, 256x128x128 voxels of seeded
+overlapping spheres (radius 3, porosity 0.40), inlet H2/H2O/Ar 0.5/0.1/0.4,
+1.0 A/cm2, 1073 K, 1 atm, FP32 populations.  A "step" is one time step of
+the whole hot path (stream + bounce-back + inlet/outlet + moments + lagged
+gradient + Maxwell-Stefan coupling + collision); MLUPS/species counts fluid
+cells x 3 species x steps / s.
+
+One JSON line on stdout (rank 0).  ``--impl reference`` times the CPU FP64
+oracle instead (a bounded sample of the same workload on the host cores).
+Launch with ``torchrun`` for N > 1: every rank runs its own replica (the
+method has no cross-replica exchange), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    "anode3d_256x128x128": "anode_3d_256x128x128",
+    "anode2d_96x48": "anode_2d_96x48",
+}
+METRIC = "MLUPS/species"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="anode3d_256x128x128", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--time-to-residual", type=float, default=0.0,
+                    help="also run to this residual from the uniform start and report the time")
+    ap.add_argument("--max-steps", type=int, default=3_000_000)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_case(name):
+    from workloads import cases
+    return getattr(cases, WORKLOADS[name])()
+
+
+def bytes_per_cell(dim, precision):
+    """Algorithmic bytes per fluid-cell update (3 species): one read and one
+    write of every population and of the mole fraction."""
+    q = 9 if dim == 2 else 19
+    es = 8 if precision == "fp64" else 4
+    return 3 * (2 * q * es + 2 * es)
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        sm = [float(r[1]) for r in self.rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) > 8:
+                for k, n in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ roofline
+def measured_peak_hbm():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("lbms_kernels.cuh", "lbms_lattice.cuh", "lbms_launch.cu"):
+        with open(os.path.join(ROOT, "paper_1809_01600_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(workload, precision):
+    """DRAM bytes per launch of the step kernel from the committed ncu summary,
+    valid only while the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(p).read().splitlines()
+    except OSError:
+        return None
+    sha = kernel_source_sha()
+    for ln in lines:
+        if ln.startswith("#") or not ln.strip():
+            continue
+        kv = dict(x.split("=", 1) for x in ln.split() if "=" in x)
+        if kv.get("kernel_sha") == sha and kv.get("workload") == workload and kv.get("precision") == precision:
+            return float(kv["dram_bytes_per_launch"])
+    return None
+
+
+# ------------------------------------------------------------- oracle
+def oracle_sample(case, budget_s, steps_hint):
+    """A z-slab of the workload (periodic), sized so one oracle step takes
+    about budget_s / steps_hint seconds."""
+    from oracle import Oracle
+    nz = case.solid.shape[0]
+    slab = max(1, min(nz, 2))
+    probe = case.with_(solid=np.ascontiguousarray(case.solid[:slab]))
+    o = Oracle(probe)
+    t = time.perf_counter()
+    o.step(1)
+    per = time.perf_counter() - t
+    per_plane = per / slab
+    target = budget_s / max(1, steps_hint)
+    planes = int(max(1, min(nz, target / max(per_plane, 1e-9))))
+    return case.with_(solid=np.ascontiguousarray(case.solid[:planes])), planes
+
+
+def run_oracle(case, steps, warmup):
+    from oracle import Oracle
+    o = Oracle(case)
+    o.step(warmup)
+    t = time.perf_counter()
+    o.step(steps)
+    return time.perf_counter() - t
+
+
+def cores_used():
+    # numpy element-wise kernels run on one thread
+    return 1
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        return main_reference(args, ws, rank)
+
+    import torch
+    if not torch.cuda.is_available():
+        print(json.dumps({"metric": METRIC, "error": "no CUDA device"}))
+        return 1
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1809_01600_gb300 import lbms as L
+    L.load()
+
+    case = make_case(args.workload)
+    nf = case.n_fluid
+    s = L.Solver.from_case(case, precision=args.precision)
+    s.set_bc(case.x_in, case.current_A_cm2)
+    stream = torch.cuda.current_stream()
+
+    # warm-up: W steps, then one graph-sized batch so the step graph exists
+    s.step(args.warmup)
+    s.step(32)
+    s.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t_dev = ms / 1e3
+    if dist:
+        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    units = nf * 3 * args.steps * ws
+    value = units / t_dev / 1e6
+
+    # dominant kernel = the step kernel, one launch per step
+    bpc = bytes_per_cell(case.dim, args.precision)
+    per_launch = t_dev / args.steps
+    achieved = nf * bpc / per_launch / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    traffic = ncu_traffic(args.workload, args.precision)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
+                "algorithmic_bytes_per_launch": nf * bpc, "kernel": "step_kernel<D3Q19,float>"
+                if case.dim == 3 and args.precision == "fp32" else "step_kernel"}
+
+    # time to residual from the uniform start (optional)
+    ttr = None
+    if args.time_to_residual > 0:
+        r0 = L.Solver.from_case(case, precision=args.precision)
+        r0.set_bc(case.x_in, case.current_A_cm2)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        n, r, st = r0.run_to_residual(args.time_to_residual, args.max_steps, raise_on_fail=False)
+        ttr_s = time.perf_counter() - t
+        eta, _ = r0.overpotential()
+        ttr = {"tol": args.time_to_residual, "steps": n, "residual": r, "seconds": round(ttr_s, 3),
+               "converged": st == L.LBMS_OK, "eta_V": eta}
+        r0.close()
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        s2 = L.Solver.from_case(case, precision=args.precision)
+        s2.set_bc(case.x_in, case.current_A_cm2)
+        s2.step(args.steps)
+        X = s2.fields()
+        eta, _ = s2.overpotential()
+        torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t
+        info = s2.info()
+        s2.close()
+        if dist:
+            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = float(tt.item())
+        e2e = {"value": round(units / t_e2e / 1e6, 2), "unit": METRIC,
+               "h2d_bytes_per_step": int(info.h2d_bytes / args.steps),
+               "d2h_bytes_per_step": int(info.d2h_bytes / args.steps),
+               "seconds": round(t_e2e, 3),
+               "scope": "create from host mask + set_bc + K steps + fields to host + overpotential"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample, planes = oracle_sample(case, 20.0, 2)
+        t_cpu = run_oracle(sample, 2, 0)
+        cpu = {"value": round(sample.n_fluid * 3 * 2 / t_cpu / 1e6, 4), "unit": METRIC,
+               "cores": cores_used(), "kind": "oracle",
+               "sample": f"2 FP64 oracle steps on the first {planes} z-planes of the same "
+                         f"{case.name} mask ({sample.n_fluid} fluid cells, periodic in z)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "config": {"workload": case.name, "lattice": "D3Q19" if case.dim == 3 else "D2Q9",
+                           "grid": list(case.solid.shape[::-1]), "fluid_cells": nf,
+                           "porosity": round(case.porosity, 4), "current_A_cm2": case.current_A_cm2,
+                           "x_in": list(case.x_in), "precision": args.precision,
+                           "parallelism": f"replicas x{ws}",
+                           "l2": "state larger than L2 (no flush needed)" if nf * bpc > 129e6 * 2
+                           else "state fits in L2"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
+                "gpu_launches": args.steps, "time_to_residual": ttr}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main_reference(args, ws, rank):
+    if rank != 0:
+        return 0
+    case = make_case(args.workload)
+    budget = 150.0
+    sample, planes = oracle_sample(case, budget, args.steps + args.warmup)
+    t = run_oracle(sample, args.steps, args.warmup)
+    value = sample.n_fluid * 3 * args.steps / t / 1e6
+    desc = (f"FP64 CPU oracle on the first {planes} z-planes of the {case.name} mask "
+            f"({sample.n_fluid} fluid cells, periodic in z), {args.steps} timed steps")
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": METRIC,
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case.name, "precision": args.precision,
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(value, 4), "unit": METRIC, "cores": cores_used(),
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(value, 4), "unit": METRIC, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

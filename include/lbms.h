@@ -1,0 +1,187 @@
+/*
+ * lbms.h -- C ABI of the GB300 solver for ternary (H2-H2O-Ar) diffusion in a
+ * porous SOFC anode: an advection-diffusion lattice Boltzmann model (one
+ * distribution per species, BGK collision, bounce-back on a voxel mask)
+ * coupled cell by cell to the Maxwell-Stefan equations through a local
+ * relaxation time (Huang, Bao, Jiang, Zhang, arXiv:1809.01600, Section 3).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns an lbms_status and never aborts; on failure
+ *    lbms_last_error(ctx) holds a one-line message for that handle.
+ *  - Host arrays passed in are read during the call only (copied); output
+ *    arrays are caller-owned host buffers of the stated size.
+ *  - Dense fields are indexed [species][z][y][x], x fastest; N = nx*ny*nz.
+ *  - Species order is (H2, H2O, Ar) = (1, 2, n) of the paper; the last one is
+ *    the reference species n of Eqs. 31-34.
+ *  - Units are SI except the current density (A/cm^2, as in Eq. 39's use).
+ *  - All device work is issued on options.stream; calls that return host
+ *    data synchronise that stream.  A handle is not thread-safe.
+ */
+#ifndef LBMS_H
+#define LBMS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbms_ctx lbms_ctx;
+
+typedef enum {
+    LBMS_OK = 0,
+    LBMS_EINVAL = 1,          /* invalid argument (message says which) */
+    LBMS_ENOMEM = 2,          /* device or host allocation failed */
+    LBMS_ECUDA = 3,           /* a CUDA call failed (message has the CUDA error) */
+    LBMS_ENOTCONVERGED = 4,   /* run_to_residual hit max_steps above tol */
+    LBMS_EUNSTABLE = 5,       /* NaN/Inf found in the mole fractions */
+    LBMS_EDEPLETED = 6,       /* outlet H2 (or inlet H2O) <= 0: Eq. 43 undefined */
+    LBMS_ESTATE = 7           /* call out of order (e.g. step before set_bc) */
+} lbms_status;
+
+enum { LBMS_FP64 = 0, LBMS_FP32 = 1 };
+enum { LBMS_COUPLING_MS = 0, LBMS_COUPLING_TAU_ONLY = 1 };
+
+/* Geometry.  dim = 2 uses D2Q9 (Eq. 2, weights Eq. 9); dim = 3 uses D3Q19.
+ * solid: N bytes, nonzero = solid voxel (half-way bounce-back, Section 3.3).
+ * periodic_x = 0: inlet nodes at x = 0 (Dirichlet, Eq. 36) and reacting
+ *   outlet nodes at x = nx-1 (flux of Eq. 39); both columns must be fluid;
+ *   grid spacing dx = length_x_m / (nx - 1).
+ * periodic_x = 1: closed box periodic in x, dx = length_x_m / nx.
+ * y and z are always periodic. */
+typedef struct {
+    int dim;
+    int nx, ny, nz;
+    const uint8_t *solid;
+    double length_x_m;
+    int periodic_x;
+} lbms_geometry;
+
+/* Species data (Table 1, Eq. 38): n must be 3. */
+typedef struct {
+    int n;
+    const double *molar_mass;     /* kg/kmol, n entries */
+    const double *fuller_volume;  /* Fuller diffusion volume, n entries */
+    const int *stoich;            /* nu_i of Eq. 38, n entries */
+    int electrons;                /* n of Eqs. 39 and 43 */
+} lbms_species;
+
+/* Binary diffusivities.  D_binary_m2s: n*n row-major (diagonal ignored), or
+ * NULL for the Fuller correlation of Eq. 40.  pore_diameter_m > 0 adds the
+ * Knudsen term of Eq. 42 through Eq. 41; <= 0 leaves it out.  eps_over_tau
+ * is the porosity/tortuosity prefactor of Eq. 41 (1.0 for resolved pores). */
+typedef struct {
+    const double *D_binary_m2s;
+    double pore_diameter_m;
+    double eps_over_tau;
+} lbms_diffusivities;
+
+/* Options; lbms_default_options fills the defaults in brackets.
+ *  precision  LBMS_FP64 or LBMS_FP32 populations and arithmetic [FP32]
+ *  coupling   LBMS_COUPLING_MS: clamped tau plus drift velocity (exact
+ *             Maxwell-Stefan flux); LBMS_COUPLING_TAU_ONLY: tau alone,
+ *             Eqs. 28-29 literally [MS]
+ *  tau_min, tau_max  clamp of Eq. 25 [1, 5]
+ *  dt_s       time step; 0 picks dt = dx^2 / (6 min D_ij,eff) [0]
+ *  check_every residual interval K of run_to_residual [100]
+ *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
+ *  alloc/free device allocator callbacks (e.g. a framework's caching
+ *             allocator); NULL = cudaMalloc/cudaFree [NULL] */
+typedef struct {
+    int precision;
+    int coupling;
+    double tau_min, tau_max;
+    double dt_s;
+    int check_every;
+    void *stream;
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *alloc_user;
+} lbms_options;
+
+typedef struct {
+    int64_t n_cells, n_fluid;
+    int q;                      /* 9 or 19 */
+    int precision;
+    double dx_m, dt_s, C_t;     /* C_t = p / RT (Section 4.1) */
+    double D_eff_m2s[9];        /* Eq. 41, row-major 3x3 */
+    double D_lat[9];            /* D_eff dt / dx^2 */
+    double q_lat[3];            /* outlet flux per node per step, Eq. 39 */
+    double x_in[3];
+    double current_A_cm2;
+    int64_t steps;              /* time steps taken since the last reset */
+    size_t device_bytes;        /* device memory held by the handle */
+    uint64_t h2d_bytes;         /* host-to-device bytes copied so far */
+    uint64_t d2h_bytes;         /* device-to-host bytes copied so far */
+} lbms_info;
+
+void lbms_default_options(lbms_options *opt);
+
+/* Builds the solver: host properties (Eqs. 40-42, C_t, dx, dt), the fluid
+ * cell list and its neighbour table, and the device state.  Nothing runs
+ * until lbms_set_bc.  *out receives the handle, or NULL on failure, when
+ * lbms_last_error(NULL) gives the reason (per thread). */
+lbms_status lbms_create(const lbms_geometry *geom, const lbms_species *species,
+                        const lbms_diffusivities *diff, double T_K, double p_Pa,
+                        const lbms_options *opt, lbms_ctx **out);
+
+/* Boundary data: inlet mole fractions (3, each >= 0, sum 1 within 1e-9;
+ * Eq. 36) and current density (A/cm^2, >= 0; Eq. 39).  The first call
+ * initialises every fluid cell to f = w X_in (Eq. 29); later calls change
+ * the boundary data and keep the state. */
+lbms_status lbms_set_bc(lbms_ctx *ctx, const double *x_inlet, double current_A_cm2);
+
+/* Restarts from a given field: X is host, 3*N dense (solid entries ignored),
+ * f = w X (Eq. 29).  Resets the step counter and the residual snapshot.
+ * Needs a prior lbms_set_bc (the boundary data). */
+lbms_status lbms_set_fields(lbms_ctx *ctx, const double *X);
+
+/* Advances nsteps >= 0 time steps (Eq. 28 with the coupling of Eqs. 19-35
+ * and the boundaries of Eqs. 36, 39).  Asynchronous: returns once the work is
+ * queued on the stream. */
+lbms_status lbms_step(lbms_ctx *ctx, int64_t nsteps);
+
+/* Residual r = max_i ||X_i - X_i,snap||_2 / (K ||X_i||_2) over fluid cells
+ * (FP64), where the snapshot is the state at the previous residual call (or
+ * the last reset); refreshes the snapshot.  K >= 1 is the number of steps
+ * since then.  LBMS_EUNSTABLE if NaN/Inf is present (residual set to inf). */
+lbms_status lbms_residual(lbms_ctx *ctx, int K, double *residual);
+
+/* Steps until the residual (checked every check_every steps) is <= tol or
+ * max_steps are taken.  LBMS_ENOTCONVERGED in the latter case;
+ * LBMS_EUNSTABLE on NaN/Inf.  steps_taken / final_residual may be NULL. */
+lbms_status lbms_run_to_residual(lbms_ctx *ctx, double tol, int64_t max_steps,
+                                 int64_t *steps_taken, double *final_residual);
+
+/* Fields of the last step on the dense grid, solid voxels zero.
+ * X: 3*N mole fractions.  u: 3*dim*N component velocities (m/s,
+ * [species][axis][z][y][x], Eq. 20) or NULL.  tau: 3*N relaxation times
+ * (Eq. 25) or NULL. */
+lbms_status lbms_get_fields(lbms_ctx *ctx, double *X, double *u, double *tau);
+
+/* Concentration overpotential (V) by Eq. 43 with X_out the mean over the
+ * outlet column (FP64) and X_in the boundary values; x_out_mean (3 doubles)
+ * may be NULL.  LBMS_EDEPLETED when a logarithm argument is <= 0. */
+lbms_status lbms_overpotential(lbms_ctx *ctx, double *eta_V, double *x_out_mean);
+
+/* Mass balance in FP64: inlet_flux[3] = net mole-fraction units per step
+ * that cross the plane between x = 0 and x = 1 toward +x (carried by the
+ * last post-collision populations); totals[3] = sum of X over fluid cells.
+ * Either pointer may be NULL. */
+lbms_status lbms_boundary_flux(lbms_ctx *ctx, double *inlet_flux, double *totals);
+
+lbms_status lbms_get_info(const lbms_ctx *ctx, lbms_info *info);
+
+/* Waits for all queued work of the handle. */
+lbms_status lbms_synchronize(lbms_ctx *ctx);
+
+void lbms_destroy(lbms_ctx *ctx);
+const char *lbms_last_error(const lbms_ctx *ctx);
+const char *lbms_status_string(lbms_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMS_H */

@@ -26,17 +26,21 @@ One time step t (all quantities in lattice units, c_s^2 = 1/3):
    B from Eq. 32, J = -B^-1 grad X per axis (Eqs. 31, 33, 34 with
    Gamma = I, Eq. 30 ideal gas), J_3 = -J_1 - J_2 (Eq. 21 with u_M = 0,
    Section 3.1), N = J (Eq. 20).
-5. Effective diffusivity, Eq. 24 read in vector form as the projection
-   D_i = -(N_i . grad X_i) / |grad X_i|^2 (equal to Eq. 24 in 1-D), blended
-   smoothly into the mixture value D_i,mix = sum_{j!=i} X_j /
-   sum_{j!=i} X_j/D_ij where the gradient vanishes:
-   D_i = (-(N_i . g_i) + eps_g^2 D_i,mix) / (|g_i|^2 + eps_g^2).
+5. Effective diffusivity, Eq. 24, with the paper's rule that each flux
+   points as its stoichiometric coefficient says (Section 3.1) and its
+   observation that the fluxes across the thin anode stay at their A/E values
+   (Sections 4.1-4.2), so that N_j / N_i = nu_j / nu_i:
+   1/D_i = sum_{j!=i} (X_j - X_i nu_j/nu_i) / D_ij.  For the inert species
+   (nu_i = 0) Eq. 24 is singular and D_i is the mixture value
+   sum_{j!=i} X_j / sum_{j!=i} X_j/D_ij.
 6. Relaxation time, Eq. 25: tau_i = D_i / c_s^2 + 1/2, clamped to
    [tau_min, tau_max]; tau_min = 1 keeps omega <= 1 (Section 2.3 (2b)).
-   The flux the clamped tau cannot carry goes into a velocity in the slot of
-   Eq. 26: v_i = (N_i + D_i^tau g_i) X_i / (X_i^2 + eps_x^2), |v_i| <= v_max,
-   D_i^tau = c_s^2 (tau_i - 1/2).  In 1-D with tau inside the clamp v_i
-   vanishes and the step is Eqs. 28-29 exactly.
+   The part of the Maxwell-Stefan flux of step 4 that the relaxation alone
+   does not carry goes into a velocity in the slot of Eq. 26:
+   v_i = (N_i + D_i^tau g_i) X_i / (X_i^2 + eps_x^2), |v_i| <= v_max,
+   D_i^tau = c_s^2 (tau_i - 1/2).  For the reacting species of the 1-D anode
+   at steady state v_i vanishes and the step is Eqs. 28-29 exactly; the inert
+   species keeps the drift that carries its Stefan drag.
 7. Collide (Eq. 28 with Eq. 29 / Eq. 26 equilibrium):
    f*_a = f_a - (f_a - w_a X_i (1 + e_a . v_i / c_s^2)) / tau_i.
 8. The moments of step 2 become the stored field used by the next gradient.
@@ -52,7 +56,7 @@ import numpy as np
 from . import lattice as _lattice
 from .gas import CS2, Scaling
 
-EPS_G = 1.0e-7        # gradient scale below which D_i tends to D_i,mix
+D_BIG = 1.0e30        # stands for an unbounded D_i (tau then sits at tau_max)
 EPS_X = 1.0e-12       # guard of 1/X_i
 MIX_DELTA = 1.0e-12   # guard of the mixture average when the others vanish
 V_MAX = 0.1           # bound on |v_i| (lattice units)
@@ -175,16 +179,20 @@ class Oracle:
         j3 = (-g3 + X3[None] * (j1 / D13 + j2 / D23)) * inv_d3
         J = np.stack([j1, j2, j3])
 
-        Dmix = np.empty_like(X)
+        nu = self.sc.stoich
+        D = np.empty_like(X)
         for i in range(3):
             o = [k for k in range(3) if k != i]
-            num = X[o[0]] + X[o[1]] + MIX_DELTA
-            den = (X[o[0]] / Dl[i, o[0]] + X[o[1]] / Dl[i, o[1]]
-                   + MIX_DELTA * 0.5 * (1.0 / Dl[i, o[0]] + 1.0 / Dl[i, o[1]]))
-            Dmix[i] = num / den
-        gg = (G * G).sum(axis=1)
-        jg = (J * G).sum(axis=1)
-        D = (-jg + EPS_G * EPS_G * Dmix) / (gg + EPS_G * EPS_G)
+            if nu[i] != 0:
+                # Eq. 24 with N_j / N_i = nu_j / nu_i
+                inv = sum((X[k] - X[i] * nu[k] / nu[i]) / Dl[i, k] for k in o)
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    D[i] = np.where(inv > 0, 1.0 / np.where(inv > 0, inv, 1.0), D_BIG)
+            else:
+                num = X[o[0]] + X[o[1]] + MIX_DELTA
+                den = (X[o[0]] / Dl[i, o[0]] + X[o[1]] / Dl[i, o[1]]
+                       + MIX_DELTA * 0.5 * (1.0 / Dl[i, o[0]] + 1.0 / Dl[i, o[1]]))
+                D[i] = num / den
         tau = np.clip(D / CS2 + 0.5, self.tau_min, self.tau_max)
         Dtau = CS2 * (tau - 0.5)
         xinv = X / (X * X + EPS_X * EPS_X)

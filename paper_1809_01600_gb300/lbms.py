@@ -1,0 +1,287 @@
+"""Python binding of the C ABI in ``include/lbms.h`` (ctypes, marshalling only).
+
+Every step of the solver runs in the CUDA library ``_build/liblbms.so``;
+this module only converts arguments.  PyTorch, when present, supplies the
+device allocator (its caching allocator) and the current CUDA stream.
+Loading fails loudly when the library is missing or cannot be built: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBMS_OK, LBMS_EINVAL, LBMS_ENOMEM, LBMS_ECUDA, LBMS_ENOTCONVERGED, LBMS_EUNSTABLE, \
+    LBMS_EDEPLETED, LBMS_ESTATE = range(8)
+LBMS_FP64, LBMS_FP32 = 0, 1
+LBMS_COUPLING_MS, LBMS_COUPLING_TAU_ONLY = 0, 1
+
+STATUS_NAMES = {0: "LBMS_OK", 1: "LBMS_EINVAL", 2: "LBMS_ENOMEM", 3: "LBMS_ECUDA",
+                4: "LBMS_ENOTCONVERGED", 5: "LBMS_EUNSTABLE", 6: "LBMS_EDEPLETED",
+                7: "LBMS_ESTATE"}
+
+EXPORTS = ("lbms_default_options", "lbms_create", "lbms_set_bc", "lbms_set_fields", "lbms_step",
+           "lbms_residual", "lbms_run_to_residual", "lbms_get_fields", "lbms_overpotential",
+           "lbms_boundary_flux", "lbms_get_info", "lbms_synchronize", "lbms_destroy",
+           "lbms_last_error", "lbms_status_string")
+
+
+class LbmsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Geometry(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("solid", C.c_void_p), ("length_x_m", C.c_double), ("periodic_x", C.c_int)]
+
+
+class Species(C.Structure):
+    _fields_ = [("n", C.c_int), ("molar_mass", C.POINTER(C.c_double)),
+                ("fuller_volume", C.POINTER(C.c_double)), ("stoich", C.POINTER(C.c_int)),
+                ("electrons", C.c_int)]
+
+
+class Diffusivities(C.Structure):
+    _fields_ = [("D_binary_m2s", C.POINTER(C.c_double)), ("pore_diameter_m", C.c_double),
+                ("eps_over_tau", C.c_double)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("coupling", C.c_int), ("tau_min", C.c_double),
+                ("tau_max", C.c_double), ("dt_s", C.c_double), ("check_every", C.c_int),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", C.c_void_p)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_fluid", C.c_int64), ("q", C.c_int),
+                ("precision", C.c_int), ("dx_m", C.c_double), ("dt_s", C.c_double),
+                ("C_t", C.c_double), ("D_eff_m2s", C.c_double * 9), ("D_lat", C.c_double * 9),
+                ("q_lat", C.c_double * 3), ("x_in", C.c_double * 3),
+                ("current_A_cm2", C.c_double), ("steps", C.c_int64),
+                ("device_bytes", C.c_size_t), ("h2d_bytes", C.c_uint64),
+                ("d2h_bytes", C.c_uint64)]
+
+
+_lib = None
+
+
+def load(build_if_needed: bool = True):
+    """Loads (building if needed) the solver library and declares its ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"solver library {_build.LIB} is missing; run __graft_entry__.build()")
+    lib = C.CDLL(_build.LIB)
+    P, D, I64 = C.c_void_p, C.POINTER(C.c_double), C.c_int64
+    st = C.c_int
+    sig = {
+        "lbms_default_options": (None, [C.POINTER(Options)]),
+        "lbms_create": (st, [C.POINTER(Geometry), C.POINTER(Species), C.POINTER(Diffusivities),
+                             C.c_double, C.c_double, C.POINTER(Options), C.POINTER(P)]),
+        "lbms_set_bc": (st, [P, D, C.c_double]),
+        "lbms_set_fields": (st, [P, D]),
+        "lbms_step": (st, [P, I64]),
+        "lbms_residual": (st, [P, C.c_int, D]),
+        "lbms_run_to_residual": (st, [P, C.c_double, I64, C.POINTER(I64), D]),
+        "lbms_get_fields": (st, [P, D, D, D]),
+        "lbms_overpotential": (st, [P, D, D]),
+        "lbms_boundary_flux": (st, [P, D, D]),
+        "lbms_get_info": (st, [P, C.POINTER(Info)]),
+        "lbms_synchronize": (st, [P]),
+        "lbms_destroy": (None, [P]),
+        "lbms_last_error": (C.c_char_p, [P]),
+        "lbms_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Solver:
+    """One solver instance on the current CUDA device (a handle of the C ABI).
+
+    ``solid`` is a bool array [z, y, x] (or [y, x] in 2-D), True = solid.
+    """
+
+    def __init__(self, solid, dim=None, length_x=2e-3, periodic_x=False, *,
+                 molar_mass=(2.016, 18.015, 39.948), fuller_volume=(6.12, 13.1, 16.2),
+                 stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
+                 eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
+                 tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
+                 torch_allocator=True):
+        lib = load()
+        self._lib = lib
+        solid = np.asarray(solid, dtype=bool)
+        if solid.ndim == 2:
+            solid = solid[None]
+        nz, ny, nx = solid.shape
+        if dim is None:
+            dim = 2 if nz == 1 else 3
+        self.shape = solid.shape
+        self.dim = dim
+        self.N = solid.size
+        mask = np.ascontiguousarray(solid.astype(np.uint8))
+        g = Geometry(dim, nx, ny, nz, mask.ctypes.data, float(length_x), int(bool(periodic_x)))
+        self._mm = np.ascontiguousarray(molar_mass, dtype=np.float64)
+        self._fv = np.ascontiguousarray(fuller_volume, dtype=np.float64)
+        self._nu = np.ascontiguousarray(stoich, dtype=np.int32)
+        sp = Species(3, _dptr(self._mm), _dptr(self._fv),
+                     self._nu.ctypes.data_as(C.POINTER(C.c_int)), int(electrons))
+        if D_binary is not None:
+            self._db = np.ascontiguousarray(D_binary, dtype=np.float64).reshape(9)
+            dptr = _dptr(self._db)
+        else:
+            dptr = None
+        df = Diffusivities(dptr, float(pore_diameter or 0.0), float(eps_over_tau))
+        o = Options()
+        lib.lbms_default_options(C.byref(o))
+        o.precision = {"fp64": LBMS_FP64, "fp32": LBMS_FP32}[precision]
+        o.coupling = {"ms": LBMS_COUPLING_MS, "tau_only": LBMS_COUPLING_TAU_ONLY}[coupling]
+        o.tau_min = float(tau_min)
+        o.tau_max = float(tau_max)
+        o.dt_s = float(dt or 0.0)
+        o.check_every = int(check_every)
+        self._keep = []
+        if stream is None or torch_allocator:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    if stream is None:
+                        stream = torch.cuda.current_stream().cuda_stream
+                    if torch_allocator:
+                        dev = torch.cuda.current_device()
+
+                        def _alloc(size, s, user):
+                            return torch.cuda.caching_allocator_alloc(int(size), dev, int(s or 0))
+
+                        def _free(ptr, size, s, user):
+                            torch.cuda.caching_allocator_delete(int(ptr))
+
+                        fa, ff = ALLOC_FN(_alloc), FREE_FN(_free)
+                        self._keep += [fa, ff]
+                        o.alloc, o.free = fa, ff
+            except ImportError:
+                pass
+        o.stream = stream or None
+        self.stream = stream or 0
+        h = C.c_void_p()
+        s = lib.lbms_create(C.byref(g), C.byref(sp), C.byref(df), float(T), float(p), C.byref(o),
+                            C.byref(h))
+        if s != LBMS_OK:
+            raise LbmsError(s, lib.lbms_last_error(None).decode())
+        self._h = h
+        self._opts = o
+
+    # -------------------------------------------------------------- helpers
+    def _check(self, s):
+        if s != LBMS_OK:
+            raise LbmsError(s, self._lib.lbms_last_error(self._h).decode())
+
+    @classmethod
+    def from_case(cls, case, **kw):
+        """Builds a solver from a workload description (duck-typed)."""
+        g = case.gas
+        args = dict(dim=case.dim, length_x=case.length_x, periodic_x=case.periodic_x,
+                    molar_mass=g.molar_mass, fuller_volume=g.fuller_volume, stoich=g.stoich,
+                    electrons=g.electrons, D_binary=g.D_binary, pore_diameter=g.pore_diameter,
+                    eps_over_tau=g.eps_over_tau, T=g.T, p=g.p)
+        args.update(kw)
+        return cls(case.solid, **args)
+
+    # ------------------------------------------------------------------ ABI
+    def set_bc(self, x_in, current_A_cm2):
+        x = np.ascontiguousarray(x_in, dtype=np.float64)
+        self._check(self._lib.lbms_set_bc(self._h, _dptr(x), float(current_A_cm2)))
+
+    def set_fields(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(3 * self.N)
+        self._check(self._lib.lbms_set_fields(self._h, _dptr(X)))
+
+    def step(self, n=1):
+        self._check(self._lib.lbms_step(self._h, int(n)))
+
+    def residual(self, K):
+        r = C.c_double()
+        self._check(self._lib.lbms_residual(self._h, int(K), C.byref(r)))
+        return r.value
+
+    def run_to_residual(self, tol, max_steps, raise_on_fail=True):
+        n = C.c_int64()
+        r = C.c_double()
+        s = self._lib.lbms_run_to_residual(self._h, float(tol), int(max_steps), C.byref(n), C.byref(r))
+        if raise_on_fail:
+            self._check(s)
+        return n.value, r.value, s
+
+    def fields(self, u=False, tau=False):
+        """Returns X [3, z, y, x] (and u [3, dim, z, y, x] in m/s, tau [3, z, y, x])."""
+        X = np.empty((3,) + self.shape)
+        U = np.empty((3, self.dim) + self.shape) if u else None
+        T = np.empty((3,) + self.shape) if tau else None
+        self._check(self._lib.lbms_get_fields(self._h, _dptr(X), _dptr(U) if u else None,
+                                              _dptr(T) if tau else None))
+        out = [X]
+        if u:
+            out.append(U)
+        if tau:
+            out.append(T)
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def overpotential(self):
+        eta = C.c_double()
+        xo = np.empty(3)
+        self._check(self._lib.lbms_overpotential(self._h, C.byref(eta), _dptr(xo)))
+        return eta.value, xo
+
+    def boundary_flux(self):
+        fl = np.empty(3)
+        tot = np.empty(3)
+        self._check(self._lib.lbms_boundary_flux(self._h, _dptr(fl), _dptr(tot)))
+        return fl, tot
+
+    def info(self):
+        i = Info()
+        self._check(self._lib.lbms_get_info(self._h, C.byref(i)))
+        return i
+
+    def synchronize(self):
+        self._check(self._lib.lbms_synchronize(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,101 @@
+"""The C ABI library builds, loads and exports every entry point of
+include/lbms.h; host-side validation answers without touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1809_01600_gb300 import lbms as L
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbms.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbms_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported():
+    lib = L.load()
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.EXPORTS)
+
+
+def test_default_options_and_status_strings():
+    lib = L.load()
+    o = L.Options()
+    lib.lbms_default_options(C.byref(o))
+    assert o.precision == L.LBMS_FP32 and o.coupling == L.LBMS_COUPLING_MS
+    assert o.tau_min == 1.0 and o.tau_max == 5.0 and o.check_every == 100
+    for s in range(8):
+        assert lib.lbms_status_string(s)
+
+
+def _create(geom_kw=None, species_kw=None, T=1073.0, p=101325.0, opt_kw=None, mask=None):
+    lib = L.load()
+    if mask is None:
+        mask = np.zeros((1, 4, 8), np.uint8)
+    gk = dict(dim=2, nx=mask.shape[2], ny=mask.shape[1], nz=mask.shape[0], solid=mask.ctypes.data,
+              length_x_m=1e-3, periodic_x=0)
+    gk.update(geom_kw or {})
+    g = L.Geometry(**gk)
+    mm = np.array([2.016, 18.015, 39.948])
+    fv = np.array([6.12, 13.1, 16.2])
+    nu = np.array([-1, 1, 0], np.int32)
+    sk = dict(n=3, molar_mass=L._dptr(mm), fuller_volume=L._dptr(fv),
+              stoich=nu.ctypes.data_as(C.POINTER(C.c_int)), electrons=2)
+    sk.update(species_kw or {})
+    sp = L.Species(**sk)
+    df = L.Diffusivities(None, 1e-6, 1.0)
+    o = L.Options()
+    lib.lbms_default_options(C.byref(o))
+    for k, v in (opt_kw or {}).items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    s = lib.lbms_create(C.byref(g), C.byref(sp), C.byref(df), T, p, C.byref(o), C.byref(h))
+    return s, h, lib.lbms_last_error(None).decode()
+
+
+@pytest.mark.parametrize("geom_kw,species_kw,extra,needle", [
+    ({"dim": 4}, None, {}, "dim"),
+    ({"nz": 2}, None, {}, "nz must be 1"),
+    ({"nx": 2}, None, {}, "nx must be >= 3"),
+    ({"solid": None}, None, {}, "solid mask"),
+    ({"length_x_m": -1.0}, None, {}, "length_x_m"),
+    (None, {"n": 4}, {}, "ternary"),
+    (None, {"electrons": 0}, {}, "electrons"),
+    (None, None, {"T": -5.0}, "T and p"),
+    (None, None, {"opt_kw": {"precision": 7}}, "precision"),
+    (None, None, {"opt_kw": {"tau_min": 0.4}}, "tau_min"),
+    (None, None, {"opt_kw": {"coupling": 3}}, "coupling"),
+])
+def test_create_rejects_invalid_input(geom_kw, species_kw, extra, needle):
+    s, h, msg = _create(geom_kw, species_kw, **extra)
+    assert s == L.LBMS_EINVAL
+    assert not h.value
+    assert needle in msg
+
+
+def test_create_rejects_blocked_boundary_columns():
+    mask = np.zeros((1, 4, 8), np.uint8)
+    mask[0, 2, 0] = 1
+    s, h, msg = _create(mask=mask)
+    assert s == L.LBMS_EINVAL and "columns must be fluid" in msg
+    mask = np.ones((1, 4, 8), np.uint8)
+    s, h, msg = _create(mask=mask, geom_kw={"periodic_x": 1})
+    assert s == L.LBMS_EINVAL and "no fluid" in msg
+
+
+def test_calls_on_null_handle_fail_cleanly():
+    lib = L.load()
+    r = C.c_double()
+    assert lib.lbms_step(None, 1) == L.LBMS_ESTATE
+    assert lib.lbms_residual(None, 1, C.byref(r)) == L.LBMS_ESTATE
+    assert lib.lbms_set_bc(None, None, 0.0) == L.LBMS_ESTATE
+    lib.lbms_destroy(None)

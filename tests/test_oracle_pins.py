@@ -275,7 +275,7 @@ def test_mirror_symmetry_2d():
     o, om = Oracle(c), Oracle(cm)
     o.step(150)
     om.step(150)
-    assert np.abs(o.X - om.X[:, :, ::-1, :]).max() < 1e-11
+    assert np.abs(o.X - om.X[:, :, ::-1, :]).max() < 1e-13
 
 
 def test_mirror_and_transpose_symmetry_3d():
@@ -290,4 +290,4 @@ def test_mirror_and_transpose_symmetry_3d():
     for solid, back in variants:
         om = Oracle(c.with_(solid=np.ascontiguousarray(solid)))
         om.step(80)
-        assert np.abs(o.X - back(om.X)).max() < 1e-11
+        assert np.abs(o.X - back(om.X)).max() < 1e-13
