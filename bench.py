@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="anode3d_256x128x128", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-residual", type=float, default=0.0,
@@ -68,8 +68,9 @@ def bytes_per_cell(dim, precision):
     """Algorithmic bytes per fluid-cell update (3 species): one read and one
     write of every population and of the mole fraction."""
     q = 9 if dim == 2 else 19
-    es = 8 if precision == "fp64" else 4
-    return 3 * (2 * q * es + 2 * es)
+    ps = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
+    xs = 8 if precision == "fp64" else 4
+    return 3 * (2 * q * ps + 2 * xs)
 
 
 # --------------------------------------------------------------- clocks
@@ -256,8 +257,10 @@ def main():
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
-                "algorithmic_bytes_per_launch": nf * bpc, "kernel": "step_kernel<D3Q19,float>"
-                if case.dim == 3 and args.precision == "fp32" else "step_kernel"}
+                "algorithmic_bytes_per_launch": nf * bpc,
+                "kernel": "step_kernel<%s,%s>" % ("D3Q19" if case.dim == 3 else "D2Q9",
+                                                 {"fp64": "double,double", "fp32": "float,float",
+                                                  "fp16": "float,__half"}[args.precision])}
 
     # time to residual from the uniform start (optional)
     ttr = None
@@ -310,7 +313,8 @@ def main():
         line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 5),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+                "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)"}[args.precision],
+                "data": "synthetic",
                 "config": {"workload": case.name, "lattice": "D3Q19" if case.dim == 3 else "D2Q9",
                            "grid": list(case.solid.shape[::-1]), "fluid_cells": nf,
                            "porosity": round(case.porosity, 4), "current_A_cm2": case.current_A_cm2,

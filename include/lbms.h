@@ -40,7 +40,7 @@ typedef enum {
     LBMS_ESTATE = 7           /* call out of order (e.g. step before set_bc) */
 } lbms_status;
 
-enum { LBMS_FP64 = 0, LBMS_FP32 = 1 };
+enum { LBMS_FP64 = 0, LBMS_FP32 = 1, LBMS_FP16 = 2 };
 enum { LBMS_COUPLING_MS = 0, LBMS_COUPLING_TAU_ONLY = 1 };
 
 /* Geometry.  dim = 2 uses D2Q9 (Eq. 2, weights Eq. 9); dim = 3 uses D3Q19.
@@ -78,7 +78,12 @@ typedef struct {
 } lbms_diffusivities;
 
 /* Options; lbms_default_options fills the defaults in brackets.
- *  precision  LBMS_FP64 or LBMS_FP32 populations and arithmetic [FP32]
+ *  precision  LBMS_FP64 or LBMS_FP32: populations, mole fractions and
+ *             arithmetic in that type; LBMS_FP16: populations stored in
+ *             FP16, mole fractions and arithmetic in FP32 [FP32].  Stored
+ *             populations and mole fractions are shifted by the equilibrium
+ *             of the first inlet composition (f - w X_ref), which keeps the
+ *             stored numbers small; results are unshifted on the way out
  *  coupling   LBMS_COUPLING_MS: clamped tau plus drift velocity (exact
  *             Maxwell-Stefan flux); LBMS_COUPLING_TAU_ONLY: tau alone,
  *             Eqs. 28-29 literally [MS]

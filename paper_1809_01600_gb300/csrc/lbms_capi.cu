@@ -205,15 +205,16 @@ void apply_bc(lbms_ctx* c) {
         for (int s = 0; s < 3; ++s) c->L.q[s] = 0.0;
 }
 
-// Copies a dense host field (3*N doubles) into X[cur] and re-initialises f.
+// Copies a dense host field (3*N doubles) into X[cur] as X - Xref and
+// re-initialises f.
 lbms_status upload_field(lbms_ctx* c, const double* X) {
     const int64_t S = c->L.S;
     const int nf = c->L.nf;
-    const size_t es = elem_size(c->L.precision);
+    const size_t es = x_size(c->L.precision);
     std::vector<unsigned char> buf(3 * (size_t)S * es, 0);
     for (int s = 0; s < 3; ++s)
         for (int i = 0; i < nf; ++i) {
-            const double v = X[(size_t)s * c->N + c->fluid_cell[i]];
+            const double v = X[(size_t)s * c->N + c->fluid_cell[i]] - c->L.xref[s];
             if (c->L.precision == LBMS_FP64)
                 reinterpret_cast<double*>(buf.data())[s * S + i] = v;
             else
@@ -349,8 +350,8 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
             if (!(sp->molar_mass[i] > 0.0)) return bail(fail(c, LBMS_EINVAL, "molar_mass must be > 0"));
     if (!(T_K > 0.0) || !(p_Pa > 0.0) || !std::isfinite(T_K) || !std::isfinite(p_Pa))
         return bail(fail(c, LBMS_EINVAL, "T and p must be finite and > 0"));
-    if (c->opt.precision != LBMS_FP64 && c->opt.precision != LBMS_FP32)
-        return bail(fail(c, LBMS_EINVAL, "precision must be LBMS_FP64 or LBMS_FP32"));
+    if (c->opt.precision != LBMS_FP64 && c->opt.precision != LBMS_FP32 && c->opt.precision != LBMS_FP16)
+        return bail(fail(c, LBMS_EINVAL, "precision must be LBMS_FP64, LBMS_FP32 or LBMS_FP16"));
     if (!(c->opt.tau_min > 0.5) || !(c->opt.tau_max >= c->opt.tau_min))
         return bail(fail(c, LBMS_EINVAL, "need 0.5 < tau_min <= tau_max"));
     if (c->opt.coupling != LBMS_COUPLING_MS && c->opt.coupling != LBMS_COUPLING_TAU_ONLY)
@@ -414,9 +415,8 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     e = cudaMallocHost(&c->host_red, 2 * kRedSlots * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "pinned readback buffer"));
 
-    const size_t es = elem_size(L.precision);
-    const size_t fbytes = (size_t)3 * c->Q * L.S * es;
-    const size_t xbytes = (size_t)3 * L.S * es;
+    const size_t fbytes = (size_t)3 * c->Q * L.S * pop_size(L.precision);
+    const size_t xbytes = (size_t)3 * L.S * x_size(L.precision);
     for (int k = 0; k < 2; ++k) {
         L.b.f[k] = dev_alloc(c, fbytes);
         L.b.X[k] = dev_alloc(c, xbytes);
@@ -459,6 +459,8 @@ lbms_status lbms_set_bc(lbms_ctx* c, const double* x_inlet, double current_A_cm2
     apply_bc(c);
     drop_graphs(c);
     if (!c->initialized) {
+        // the stored state is shifted by the first inlet composition
+        for (int s = 0; s < 3; ++s) c->L.xref[s] = c->x_in[s];
         std::vector<double> X(3 * (size_t)c->N, 0.0);
         for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * c->N, X.begin() + (s + 1) * c->N, c->x_in[s]);
         return upload_field(c, X.data());
@@ -527,7 +529,7 @@ lbms_status lbms_get_fields(lbms_ctx* c, double* X, double* u, double* tau) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
     const int64_t S = c->L.S;
     const int nf = c->L.nf;
-    const size_t es = elem_size(c->L.precision);
+    const size_t es = x_size(c->L.precision);
     auto to_double = [&](const std::vector<unsigned char>& b, int64_t idx) {
         return c->L.precision == LBMS_FP64 ? reinterpret_cast<const double*>(b.data())[idx]
                                            : (double)reinterpret_cast<const float*>(b.data())[idx];
@@ -539,7 +541,7 @@ lbms_status lbms_get_fields(lbms_ctx* c, double* X, double* u, double* tau) {
         c->d2h += b.size();
         std::fill(X, X + 3 * c->N, 0.0);
         for (int s = 0; s < 3; ++s)
-            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = to_double(b, s * S + i);
+            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = c->L.xref[s] + to_double(b, s * S + i);
     }
     if (u || tau) {
         if (!c->L.b.fields) {

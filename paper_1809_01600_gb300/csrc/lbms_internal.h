@@ -14,9 +14,9 @@ constexpr int kRedBoundary = 1;        // slot of the boundary sums
 constexpr int kRedMaxBlocks = 1216;    // 152 SMs x 8 resident blocks of 256 threads
 
 struct DevBuffers {
-    void* f[2] = {nullptr, nullptr};   // post-collision populations, [3][Q][S]
-    void* X[2] = {nullptr, nullptr};   // mole fractions, [3][S]
-    void* snap = nullptr;              // residual snapshot, [3][S]
+    void* f[2] = {nullptr, nullptr};   // post-collision populations minus w Xref, [3][Q][S]
+    void* X[2] = {nullptr, nullptr};   // mole fractions minus Xref, [3][S]
+    void* snap = nullptr;              // residual snapshot (minus Xref), [3][S]
     int* nbr = nullptr;                // [Q-1][S]
     int* rows = nullptr;               // [3][nrows]: x = 0, x = 1, x = nx-1 cell per row (-1 if solid)
     double* red_partials = nullptr;    // [kRedMaxBlocks][kRedSlots]
@@ -27,12 +27,13 @@ struct DevBuffers {
 
 struct Launch {
     int dim = 2;
-    int precision = 1;                 // 0 = FP64, 1 = FP32
+    int precision = 1;                 // 0 = FP64, 1 = FP32, 2 = FP16 populations / FP32 compute
     int64_t S = 0;                     // padded row stride (elements)
     int nf = 0;                        // fluid cells
     int nrows = 0;                     // ny * nz
     int cur = 0;                       // lattice holding the latest post-collision state
     DevBuffers b;
+    double xref[3] = {0, 0, 0};        // shift of the stored state
     double xin[3] = {0, 0, 0};
     double q[3] = {0, 0, 0};
     double D12 = 1, D13 = 1, D23 = 1;  // lattice binary diffusivities
@@ -42,7 +43,8 @@ struct Launch {
     int sm_count = 152;
 };
 
-size_t elem_size(int precision);
+size_t pop_size(int precision);    // bytes per stored population
+size_t x_size(int precision);      // bytes per stored mole fraction
 int residual_blocks(const Launch& L);
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st);

@@ -3,12 +3,19 @@
 //
 // Storage (all compact over the fluid cells, x-fastest order, padded row
 // stride S, a multiple of 32 elements):
-//   f[s][k][i]   post-collision populations, two lattices (pull streaming)
-//   X[s][i]      mole fractions of a step, two buffers (this step / previous)
+//   f[s][k][i]   post-collision populations, two lattices (pull streaming),
+//                stored shifted: f - w_k Xref_s (Xref = a fixed reference
+//                composition), in FP64, FP32 or FP16 (FP16 scaled by 2^10)
+//   X[s][i]      mole fractions of a step minus Xref, two buffers (this step /
+//                previous), FP64 or FP32
 //   nbr[k-1][i]  fluid index of the source cell x - e_k, or an NB_* code
+// The shift is exact algebra (sum_k w_k = 1, w_k = w_opp(k)); it keeps the
+// stored numbers near zero so that their rounding error scales with the
+// departure from Xref rather than with X itself.
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "lbms_lattice.cuh"
@@ -31,17 +38,33 @@ struct MsConst {
     int drift;            // 1: drift velocity carries the Maxwell-Stefan flux tau does not
 };
 
-template <typename T>
+// Population storage: P = T, or __half holding (f - w Xref) * 2^10.
+constexpr float kHalfScale = 1024.0f;
+constexpr float kHalfInvScale = 1.0f / 1024.0f;
+
+template <typename T, typename P>
+struct Pop {
+    __device__ __forceinline__ static T load(const P* p) { return T(*p); }
+    __device__ __forceinline__ static void store(P* p, T v) { *p = P(v); }
+};
+template <>
+struct Pop<float, __half> {
+    __device__ __forceinline__ static float load(const __half* p) { return __half2float(*p) * kHalfInvScale; }
+    __device__ __forceinline__ static void store(__half* p, float v) { *p = __float2half_rn(v * kHalfScale); }
+};
+
+template <typename T, typename P>
 struct StepParams {
-    const T* __restrict__ fin;
-    T* __restrict__ fout;
+    const P* __restrict__ fin;
+    P* __restrict__ fout;
     const T* __restrict__ xprev;
     T* __restrict__ xnext;
     const int* __restrict__ nbr;
     int64_t S;
     int nf;
-    T xin[3];
-    T qout[3];
+    T xref[3];      // shift of the stored populations and mole fractions
+    T dxin[3];      // inlet mole fractions minus xref (Eq. 36)
+    T qout[3];      // outlet flux per node per step (Eq. 39)
     MsConst<T> c;
 };
 
@@ -146,8 +169,9 @@ __device__ __forceinline__ void ms_coupling(const T (&X)[3], const T (&g)[3][DIM
 // One time step for every fluid cell (one thread per cell):
 // pull-stream with bounce-back / inlet / outlet, moments, lagged gradient,
 // coupling, BGK collision, store post-collision populations and X.
-template <class L, typename T>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
+// All population arithmetic is on shifted values g_k = f_k - w_k Xref.
+template <class L, typename T, typename P>
+__global__ void __launch_bounds__(256) step_kernel(const StepParams<T, P> p) {
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -167,15 +191,15 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int src = nb[k];
-            const T* row = p.fin + (int64_t)(s * Q + k) * S;
-            const T* orow = p.fin + (int64_t)(s * Q + opp<L>(k)) * S;
+            const P* row = p.fin + (int64_t)(s * Q + k) * S;
+            const P* orow = p.fin + (int64_t)(s * Q + opp<L>(k)) * S;
             T val;
             if (src >= 0)
-                val = row[src];
+                val = Pop<T, P>::load(row + src);
             else if (src == NB_SOLID)
-                val = orow[i];
+                val = Pop<T, P>::load(orow + i);
             else if (src == NB_OUTLET)
-                val = orow[i] - (T(weight<L>(opp<L>(k))) / wx) * p.qout[s];
+                val = Pop<T, P>::load(orow + i) - (T(weight<L>(opp<L>(k))) / wx) * p.qout[s];
             else
                 val = T(0);
             f[s][k] = val;
@@ -183,18 +207,19 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
-                f[s][k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * p.xin[s] - f[s][opp<L>(k)];
+                f[s][k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * p.dxin[s] - f[s][opp<L>(k)];
         }
     }
 
-    // 2. moments
-    T X[3];
+    // 2. moments (shifted: Xs = X - Xref)
+    T Xs[3], X[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         T acc = T(0);
 #pragma unroll
         for (int k = 0; k < Q; ++k) acc += f[s][k];
-        X[s] = acc;
+        Xs[s] = acc;
+        X[s] = p.xref[s] + acc;
     }
 
     // 3-6. lagged gradient and Maxwell-Stefan coupling
@@ -203,7 +228,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
     T tau[3], v[3][DIM];
     ms_coupling<T, DIM>(X, g, p.c, tau, v, nullptr);
 
-    // 7. BGK collision towards w X (1 + e.v / c_s^2), store
+    // 7. BGK collision towards w X (1 + e.v / c_s^2), shifted by w Xref, store
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const T it = T(1) / tau[s];
@@ -212,10 +237,11 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
             T ev = T(0);
 #pragma unroll
             for (int d = 0; d < DIM; ++d) ev += T(L::e(k, d)) * v[s][d];
-            const T feq = T(weight<L>(k)) * X[s] * (T(1) + T(3) * ev);
-            p.fout[(int64_t)(s * Q + k) * S + i] = f[s][k] - (f[s][k] - feq) * it;
+            const T w = T(weight<L>(k));
+            const T geq = w * Xs[s] + T(3) * w * X[s] * ev;
+            Pop<T, P>::store(p.fout + (int64_t)(s * Q + k) * S + i, f[s][k] - (f[s][k] - geq) * it);
         }
-        p.xnext[s * S + i] = X[s];
+        p.xnext[s * S + i] = Xs[s];
     }
 }
 
@@ -224,7 +250,7 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T> p) {
 // stored fields (X of the step and of the step before).
 template <class L, typename T>
 __global__ void fields_kernel(const T* __restrict__ xcur, const T* __restrict__ xprev,
-                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<T> c,
+                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<T> c, T xr0, T xr1, T xr2,
                               T* __restrict__ tau_out, T* __restrict__ u_out) {
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
@@ -234,9 +260,10 @@ __global__ void fields_kernel(const T* __restrict__ xcur, const T* __restrict__ 
     nb[0] = i;
 #pragma unroll
     for (int k = 1; k < Q; ++k) nb[k] = nbr[(int64_t)(k - 1) * S + i];
+    const T xr[3] = {xr0, xr1, xr2};
     T X[3];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) X[s] = xcur[s * S + i];
+    for (int s = 0; s < 3; ++s) X[s] = xr[s] + xcur[s * S + i];
     T g[3][DIM];
     lagged_gradient<L, T>(xprev, S, i, nb, g);
     T tau[3], v[3][DIM], u[3][DIM];
@@ -249,20 +276,20 @@ __global__ void fields_kernel(const T* __restrict__ xcur, const T* __restrict__ 
     }
 }
 
-// f = w X (Eq. 29 equilibrium) in the current lattice; both X buffers and the
-// residual snapshot take X.
-template <class L, typename T>
-__global__ void init_kernel(T* __restrict__ f, T* __restrict__ x0, T* __restrict__ x1, T* __restrict__ snap,
+// f = w X (Eq. 29 equilibrium) in the current lattice, i.e. stored w (X - Xref);
+// both X buffers and the residual snapshot take X - Xref (already in x0).
+template <class L, typename T, typename P>
+__global__ void init_kernel(P* __restrict__ f, const T* __restrict__ x0, T* __restrict__ x1, T* __restrict__ snap,
                             int64_t S, int nf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        const T X = x0[s * S + i];
-        x1[s * S + i] = X;
-        snap[s * S + i] = X;
+        const T Xs = x0[s * S + i];
+        x1[s * S + i] = Xs;
+        snap[s * S + i] = Xs;
 #pragma unroll
-        for (int k = 0; k < L::Q; ++k) f[(int64_t)(s * L::Q + k) * S + i] = T(weight<L>(k)) * X;
+        for (int k = 0; k < L::Q; ++k) Pop<T, P>::store(f + (int64_t)(s * L::Q + k) * S + i, T(weight<L>(k)) * Xs);
     }
 }
 
@@ -330,21 +357,25 @@ __device__ __forceinline__ void reduce_to_out(double (&acc)[NV], double* __restr
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Residual sums over fluid cells in FP64: out[0..2] = sum (X - snap)^2,
-// out[3..5] = sum X^2, out[6..8] = sum X, out[9] = count of non-finite X.
-// When update != 0 the snapshot takes X.  Grid-stride, persistent grid.
+// Residual sums over fluid cells in FP64 (X = Xref + stored value):
+// out[0..2] = sum (X - snap)^2, out[3..5] = sum X^2, out[6..8] = sum X,
+// out[9] = count of non-finite X.  When update != 0 the snapshot takes X.
+// Grid-stride over a persistent grid.
 template <typename T>
 __global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ X, T* __restrict__ snap,
-                                                       int64_t S, int nf, int update, double* __restrict__ partials,
+                                                       int64_t S, int nf, int update, double xr0, double xr1,
+                                                       double xr2, double* __restrict__ partials,
                                                        unsigned int* __restrict__ counter, double* __restrict__ out) {
+    const double xr[3] = {xr0, xr1, xr2};
     double acc[10];
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const double x = (double)X[s * S + i];
-            const double d = x - (double)snap[s * S + i];
+            const double xs = (double)X[s * S + i];
+            const double d = xs - (double)snap[s * S + i];
+            const double x = xr[s] + xs;
             acc[s] += d * d;
             acc[3 + s] += x * x;
             acc[6 + s] += x;
@@ -358,14 +389,15 @@ __global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ X, 
 // Boundary sums in FP64 over the ny*nz rows: out[0..2] = net flux toward +x
 // through the plane between x = 0 and x = 1 (post-collision populations of
 // the last step), out[3..5] = sum of X over the outlet column.
-template <class L, typename T>
-__global__ void __launch_bounds__(256) boundary_kernel(const T* __restrict__ f, const T* __restrict__ X,
+template <class L, typename T, typename P>
+__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ f, const T* __restrict__ X,
                                                        const int* __restrict__ nbr, int64_t S,
                                                        const int* __restrict__ row_x0, const int* __restrict__ row_x1,
-                                                       const int* __restrict__ row_out, int nrows,
-                                                       double* __restrict__ partials, unsigned int* __restrict__ counter,
-                                                       double* __restrict__ out) {
+                                                       const int* __restrict__ row_out, int nrows, double xr0,
+                                                       double xr1, double xr2, double* __restrict__ partials,
+                                                       unsigned int* __restrict__ counter, double* __restrict__ out) {
     constexpr int Q = L::Q;
+    const double xr[3] = {xr0, xr1, xr2};
     double acc[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) acc[v] = 0.0;
@@ -376,22 +408,25 @@ __global__ void __launch_bounds__(256) boundary_kernel(const T* __restrict__ f, 
 #pragma unroll
         for (int k = 1; k < Q; ++k) {
             const int ex = L::e(k, 0);
+            const double w = weight<L>(k);
             if (ex == 1 && i0 >= 0) {
                 // f*_k at x = 0 reaches x + e_k when that cell (the source of opp(k)) is fluid
                 if (nbr[(int64_t)(opp<L>(k) - 1) * S + i0] >= 0) {
 #pragma unroll
-                    for (int s = 0; s < 3; ++s) acc[s] += (double)f[(int64_t)(s * Q + k) * S + i0];
+                    for (int s = 0; s < 3; ++s)
+                        acc[s] += (double)Pop<T, P>::load(f + (int64_t)(s * Q + k) * S + i0) + w * xr[s];
                 }
             } else if (ex == -1 && i1 >= 0) {
                 if (nbr[(int64_t)(opp<L>(k) - 1) * S + i1] >= 0) {
 #pragma unroll
-                    for (int s = 0; s < 3; ++s) acc[s] -= (double)f[(int64_t)(s * Q + k) * S + i1];
+                    for (int s = 0; s < 3; ++s)
+                        acc[s] -= (double)Pop<T, P>::load(f + (int64_t)(s * Q + k) * S + i1) + w * xr[s];
                 }
             }
         }
         if (io >= 0) {
 #pragma unroll
-            for (int s = 0; s < 3; ++s) acc[3 + s] += (double)X[s * S + io];
+            for (int s = 0; s < 3; ++s) acc[3 + s] += xr[s] + (double)X[s * S + io];
         }
     }
     reduce_to_out<6>(acc, partials, counter, out);

@@ -1,4 +1,5 @@
-// Kernel instantiations and launch wrappers (D2Q9 / D3Q19 x FP64 / FP32).
+// Kernel instantiations and launch wrappers (D2Q9 / D3Q19 x FP64 / FP32 /
+// FP16-stored populations with FP32 arithmetic).
 #include <algorithm>
 
 #include "lbms_internal.h"
@@ -36,79 +37,86 @@ MsConst<T> make_const(const Launch& L) {
     return c;
 }
 
-template <class Lat, typename T>
+template <class Lat, typename T, typename P>
 cudaError_t step_t(const Launch& L, cudaStream_t st) {
-    StepParams<T> p;
-    p.fin = static_cast<const T*>(L.b.f[L.cur]);
-    p.fout = static_cast<T*>(L.b.f[L.cur ^ 1]);
+    StepParams<T, P> p;
+    p.fin = static_cast<const P*>(L.b.f[L.cur]);
+    p.fout = static_cast<P*>(L.b.f[L.cur ^ 1]);
     p.xprev = static_cast<const T*>(L.b.X[L.cur]);
     p.xnext = static_cast<T*>(L.b.X[L.cur ^ 1]);
     p.nbr = L.b.nbr;
     p.S = L.S;
     p.nf = L.nf;
     for (int s = 0; s < 3; ++s) {
-        p.xin[s] = T(L.xin[s]);
+        p.xref[s] = T(L.xref[s]);
+        p.dxin[s] = T(L.xin[s] - L.xref[s]);
         p.qout[s] = T(L.q[s]);
     }
     p.c = make_const<T>(L);
     const int grid = (L.nf + kBlock - 1) / kBlock;
-    step_kernel<Lat, T><<<grid, kBlock, 0, st>>>(p);
+    step_kernel<Lat, T, P><<<grid, kBlock, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T>
+template <class Lat, typename T, typename P>
 cudaError_t init_t(const Launch& L, cudaStream_t st) {
     const int grid = (L.nf + kBlock - 1) / kBlock;
-    init_kernel<Lat, T><<<grid, kBlock, 0, st>>>(static_cast<T*>(L.b.f[L.cur]), static_cast<T*>(L.b.X[L.cur]),
-                                                 static_cast<T*>(L.b.X[L.cur ^ 1]), static_cast<T*>(L.b.snap), L.S,
-                                                 L.nf);
+    init_kernel<Lat, T, P><<<grid, kBlock, 0, st>>>(static_cast<P*>(L.b.f[L.cur]), static_cast<const T*>(L.b.X[L.cur]),
+                                                    static_cast<T*>(L.b.X[L.cur ^ 1]), static_cast<T*>(L.b.snap), L.S,
+                                                    L.nf);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T>
+template <class Lat, typename T, typename P>
 cudaError_t fields_t(const Launch& L, cudaStream_t st) {
     const int grid = (L.nf + kBlock - 1) / kBlock;
     T* base = static_cast<T*>(L.b.fields);
     fields_kernel<Lat, T><<<grid, kBlock, 0, st>>>(static_cast<const T*>(L.b.X[L.cur]),
                                                    static_cast<const T*>(L.b.X[L.cur ^ 1]), L.b.nbr, L.S, L.nf,
-                                                   make_const<T>(L), base, base + 3 * L.S);
+                                                   make_const<T>(L), T(L.xref[0]), T(L.xref[1]), T(L.xref[2]), base,
+                                                   base + 3 * L.S);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t residual_t(const Launch& L, int update, cudaStream_t st) {
     residual_kernel<T><<<residual_blocks(L), kBlock, 0, st>>>(
-        static_cast<const T*>(L.b.X[L.cur]), static_cast<T*>(L.b.snap), L.S, L.nf, update, L.b.red_partials,
-        L.b.red_counter + kRedResidual, L.b.red_out + kRedResidual * kRedSlots);
+        static_cast<const T*>(L.b.X[L.cur]), static_cast<T*>(L.b.snap), L.S, L.nf, update, L.xref[0], L.xref[1],
+        L.xref[2], L.b.red_partials, L.b.red_counter + kRedResidual, L.b.red_out + kRedResidual * kRedSlots);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T>
+template <class Lat, typename T, typename P>
 cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
     const int blocks = std::max(1, std::min((L.nrows + kBlock - 1) / kBlock, kRedMaxBlocks / 2));
-    boundary_kernel<Lat, T><<<blocks, kBlock, 0, st>>>(
-        static_cast<const T*>(L.b.f[L.cur]), static_cast<const T*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
-        L.b.rows + L.nrows, L.b.rows + 2 * L.nrows, L.nrows, L.b.red_partials + kRedMaxBlocks * kRedSlots / 2,
-        L.b.red_counter + kRedBoundary, L.b.red_out + kRedBoundary * kRedSlots);
+    boundary_kernel<Lat, T, P><<<blocks, kBlock, 0, st>>>(
+        static_cast<const P*>(L.b.f[L.cur]), static_cast<const T*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
+        L.b.rows + L.nrows, L.b.rows + 2 * L.nrows, L.nrows, L.xref[0], L.xref[1], L.xref[2],
+        L.b.red_partials + kRedMaxBlocks * kRedSlots / 2, L.b.red_counter + kRedBoundary,
+        L.b.red_out + kRedBoundary * kRedSlots);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t elem_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
+size_t pop_size(int precision) { return precision == 0 ? sizeof(double) : (precision == 1 ? sizeof(float) : 2); }
+size_t x_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
 
 int residual_blocks(const Launch& L) {
     const int want = (L.nf + kBlock - 1) / kBlock;
     return std::max(1, std::min(want, std::min(kRedMaxBlocks / 2, 4 * L.sm_count)));
 }
 
-#define LBMS_DISPATCH(FN, ...)                                                     \
-    do {                                                                           \
-        if (L.dim == 2)                                                            \
-            return L.precision == 0 ? FN<D2Q9, double>(__VA_ARGS__)                \
-                                    : FN<D2Q9, float>(__VA_ARGS__);                \
-        return L.precision == 0 ? FN<D3Q19, double>(__VA_ARGS__)                   \
-                                : FN<D3Q19, float>(__VA_ARGS__);                   \
+#define LBMS_DISPATCH(FN, ...)                                                              \
+    do {                                                                                    \
+        if (L.dim == 2) {                                                                   \
+            if (L.precision == 0) return FN<D2Q9, double, double>(__VA_ARGS__);             \
+            if (L.precision == 1) return FN<D2Q9, float, float>(__VA_ARGS__);               \
+            return FN<D2Q9, float, __half>(__VA_ARGS__);                                    \
+        }                                                                                   \
+        if (L.precision == 0) return FN<D3Q19, double, double>(__VA_ARGS__);                \
+        if (L.precision == 1) return FN<D3Q19, float, float>(__VA_ARGS__);                  \
+        return FN<D3Q19, float, __half>(__VA_ARGS__);                                       \
     } while (0)
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(step_t, L, st); }

@@ -17,7 +17,7 @@ from . import build as _build
 
 LBMS_OK, LBMS_EINVAL, LBMS_ENOMEM, LBMS_ECUDA, LBMS_ENOTCONVERGED, LBMS_EUNSTABLE, \
     LBMS_EDEPLETED, LBMS_ESTATE = range(8)
-LBMS_FP64, LBMS_FP32 = 0, 1
+LBMS_FP64, LBMS_FP32, LBMS_FP16 = 0, 1, 2
 LBMS_COUPLING_MS, LBMS_COUPLING_TAU_ONLY = 0, 1
 
 STATUS_NAMES = {0: "LBMS_OK", 1: "LBMS_EINVAL", 2: "LBMS_ENOMEM", 3: "LBMS_ECUDA",
@@ -157,7 +157,7 @@ class Solver:
         df = Diffusivities(dptr, float(pore_diameter or 0.0), float(eps_over_tau))
         o = Options()
         lib.lbms_default_options(C.byref(o))
-        o.precision = {"fp64": LBMS_FP64, "fp32": LBMS_FP32}[precision]
+        o.precision = {"fp64": LBMS_FP64, "fp32": LBMS_FP32, "fp16": LBMS_FP16}[precision]
         o.coupling = {"ms": LBMS_COUPLING_MS, "tau_only": LBMS_COUPLING_TAU_ONLY}[coupling]
         o.tau_min = float(tau_min)
         o.tau_max = float(tau_max)

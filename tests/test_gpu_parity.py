@@ -4,7 +4,9 @@ the same seeded inputs, element by element.
 Tolerances: FP64 kernels agree with the oracle to rounding (the two sum in
 different orders), bounded here by 1e-11 absolute on mole fractions after up
 to a few thousand steps; FP32 kernels to 1e-6 absolute on mole fractions
-(the stated target for single precision), tau to 1e-4 relative.
+(the stated single-precision target), tau to 5e-4; FP16-stored populations
+(FP32 arithmetic) to 2e-5 absolute on mole fractions over a few hundred
+steps and 1e-4 relative on the overpotential at steady state.
 """
 import numpy as np
 import pytest
@@ -16,6 +18,7 @@ pytestmark = pytest.mark.gpu
 
 FP64_TOL = 1e-11
 FP32_TOL = 1e-6
+FP16_TOL = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -186,6 +189,22 @@ def test_fp32_parity_2d(lbms):
     assert np.abs(X - o.X)[:, f].max() <= FP32_TOL
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fp16_step_parity(lbms, dim):
+    """FP16-stored populations (FP32 arithmetic) against the FP64 oracle."""
+    if dim == 2:
+        case = cases.porous((40, 48), radius=3, porosity=0.55, seed=21, current_A_cm2=1.5)
+    else:
+        case = cases.anode_3d_small()
+    X0 = smooth_field(case.solid.shape, 12, amp=0.02)
+    s, o = make_pair(lbms, case, "fp16", X0=X0)
+    s.step(300)
+    o.step(300)
+    X = s.fields()
+    f = ~case.solid
+    assert np.abs(X - o.X)[:, f].max() <= FP16_TOL
+
+
 # ------------------------------------------------------ steady states
 def test_steady_state_parity_and_flux_balance(lbms):
     """Both sides run to residual 1e-12 (FP64); fields, eta and the inlet flux
@@ -207,6 +226,26 @@ def test_steady_state_parity_and_flux_balance(lbms):
     assert flux[1] == pytest.approx(info.q_lat[1] * n_out, rel=1e-7)
     assert abs(flux[2]) < 1e-7 * abs(info.q_lat[0]) * n_out
     assert np.allclose(flux, o.plane_flux()[:, 0], rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision,xtol", [("fp32", FP32_TOL), ("fp16", None)])
+def test_steady_state_single_and_half_precision(lbms, precision, xtol):
+    """Steady state in FP32 (mole fractions within 1e-6 of the FP64 oracle)
+    and with FP16 storage (overpotential within 1e-4 relative)."""
+    case = cases.porous((12, 20), radius=2, porosity=0.6, seed=7, current_A_cm2=1.0)
+    s = lbms.Solver.from_case(case, precision=precision)
+    s.set_bc(case.x_in, case.current_A_cm2)
+    n, r, st = s.run_to_residual(1e-10, 400000, raise_on_fail=False)
+    o = Oracle(case)
+    o.run_to_residual(1e-12, 400000, 100)
+    X = s.fields()
+    f = ~case.solid
+    err = np.abs(X - o.X)[:, f].max()
+    eta, _ = s.overpotential()
+    assert eta == pytest.approx(o.overpotential(), rel=1e-4)
+    if xtol is not None:
+        assert st == lbms.LBMS_OK and r <= 1e-10
+        assert err <= xtol
 
 
 def test_lattice_constants_match_oracle(lbms):
@@ -247,7 +286,7 @@ def test_full_size_fp32_closed_box_conservation(lbms):
     _, tot0 = s.boundary_flux()
     s.step(1000)
     _, tot = s.boundary_flux()
-    assert np.allclose(tot, tot0, rtol=2e-6)
+    assert np.allclose(tot, tot0, rtol=1e-6)
 
 
 # ------------------------------------------------------ error handling
