@@ -66,10 +66,11 @@ def make_case(name):
 
 def bytes_per_cell(dim, precision):
     """Algorithmic bytes per fluid-cell update (3 species): one read and one
-    write of every population and of the mole fraction."""
+    write of every stored population (non-equilibrium part, 8/4/2 bytes) and
+    of the mole fraction (FP64, or an 8-byte double-float pair)."""
     q = 9 if dim == 2 else 19
     ps = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
-    xs = 8 if precision == "fp64" else 4
+    xs = 8
     return 3 * (2 * q * ps + 2 * xs)
 
 
@@ -259,8 +260,8 @@ def main():
                 "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
                 "algorithmic_bytes_per_launch": nf * bpc,
                 "kernel": "step_kernel<%s,%s>" % ("D3Q19" if case.dim == 3 else "D2Q9",
-                                                 {"fp64": "double,double", "fp32": "float,float",
-                                                  "fp16": "float,__half"}[args.precision])}
+                                                 {"fp64": "double,double", "fp32": "float2,float",
+                                                  "fp16": "float2,__half"}[args.precision])}
 
     # time to residual from the uniform start (optional)
     ttr = None

@@ -78,12 +78,11 @@ typedef struct {
 } lbms_diffusivities;
 
 /* Options; lbms_default_options fills the defaults in brackets.
- *  precision  LBMS_FP64 or LBMS_FP32: populations, mole fractions and
- *             arithmetic in that type; LBMS_FP16: populations stored in
- *             FP16, mole fractions and arithmetic in FP32 [FP32].  Stored
- *             populations and mole fractions are shifted by the equilibrium
- *             of the first inlet composition (f - w X_ref), which keeps the
- *             stored numbers small; results are unshifted on the way out
+ *  precision  LBMS_FP64: state and arithmetic in FP64.  LBMS_FP32: FP32
+ *             arithmetic, non-equilibrium populations in FP32 and mole
+ *             fractions as double-float pairs (two FP32 words), which keeps
+ *             steady states free of FP32 stagnation.  LBMS_FP16: as FP32
+ *             with the non-equilibrium populations stored in FP16 [FP32]
  *  coupling   LBMS_COUPLING_MS: clamped tau plus drift velocity (exact
  *             Maxwell-Stefan flux); LBMS_COUPLING_TAU_ONLY: tau alone,
  *             Eqs. 28-29 literally [MS]

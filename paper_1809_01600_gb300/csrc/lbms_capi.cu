@@ -205,21 +205,30 @@ void apply_bc(lbms_ctx* c) {
         for (int s = 0; s < 3; ++s) c->L.q[s] = 0.0;
 }
 
-// Copies a dense host field (3*N doubles) into X[cur] as X - Xref and
-// re-initialises f.
+// Mole fractions in the device format: double, or a double-float pair.
+void put_x(int precision, unsigned char* buf, int64_t idx, double v) {
+    if (precision == LBMS_FP64) {
+        reinterpret_cast<double*>(buf)[idx] = v;
+    } else {
+        const float hi = (float)v;
+        reinterpret_cast<float*>(buf)[2 * idx] = hi;
+        reinterpret_cast<float*>(buf)[2 * idx + 1] = (float)(v - (double)hi);
+    }
+}
+
+double get_x(int precision, const unsigned char* buf, int64_t idx) {
+    if (precision == LBMS_FP64) return reinterpret_cast<const double*>(buf)[idx];
+    return (double)reinterpret_cast<const float*>(buf)[2 * idx] + (double)reinterpret_cast<const float*>(buf)[2 * idx + 1];
+}
+
+// Copies a dense host field (3*N doubles) into X[cur] and restarts from the
+// equilibrium f = w X (h = 0).
 lbms_status upload_field(lbms_ctx* c, const double* X) {
     const int64_t S = c->L.S;
     const int nf = c->L.nf;
-    const size_t es = x_size(c->L.precision);
-    std::vector<unsigned char> buf(3 * (size_t)S * es, 0);
+    std::vector<unsigned char> buf(3 * (size_t)S * x_size(c->L.precision), 0);
     for (int s = 0; s < 3; ++s)
-        for (int i = 0; i < nf; ++i) {
-            const double v = X[(size_t)s * c->N + c->fluid_cell[i]] - c->L.xref[s];
-            if (c->L.precision == LBMS_FP64)
-                reinterpret_cast<double*>(buf.data())[s * S + i] = v;
-            else
-                reinterpret_cast<float*>(buf.data())[s * S + i] = (float)v;
-        }
+        for (int i = 0; i < nf; ++i) put_x(c->L.precision, buf.data(), s * S + i, X[(size_t)s * c->N + c->fluid_cell[i]]);
     CK(cudaMemcpyAsync(c->L.b.X[c->L.cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream),
        "upload mole fractions");
     c->h2d += buf.size();
@@ -421,7 +430,8 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
         L.b.f[k] = dev_alloc(c, fbytes);
         L.b.X[k] = dev_alloc(c, xbytes);
     }
-    L.b.snap = dev_alloc(c, xbytes);
+    const size_t sbytes = (size_t)3 * L.S * sizeof(double);
+    L.b.snap = static_cast<double*>(dev_alloc(c, sbytes));
     L.b.nbr = static_cast<int*>(dev_alloc(c, (size_t)(c->Q - 1) * L.S * sizeof(int)));
     L.b.rows = static_cast<int*>(dev_alloc(c, 3 * (size_t)nrows * sizeof(int)));
     L.b.red_partials = static_cast<double*>(dev_alloc(c, (size_t)kRedMaxBlocks * kRedSlots * sizeof(double)));
@@ -442,7 +452,7 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     if (e == cudaSuccess) e = cudaMemsetAsync(L.b.red_counter, 0, 4 * sizeof(unsigned int), c->stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.f[k], 0, fbytes, c->stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.X[k], 0, xbytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.b.snap, 0, xbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.b.snap, 0, sbytes, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload of the neighbour table"));
     c->h2d += nbr.size() * sizeof(int) + rows.size() * sizeof(int);
@@ -459,8 +469,6 @@ lbms_status lbms_set_bc(lbms_ctx* c, const double* x_inlet, double current_A_cm2
     apply_bc(c);
     drop_graphs(c);
     if (!c->initialized) {
-        // the stored state is shifted by the first inlet composition
-        for (int s = 0; s < 3; ++s) c->L.xref[s] = c->x_in[s];
         std::vector<double> X(3 * (size_t)c->N, 0.0);
         for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * c->N, X.begin() + (s + 1) * c->N, c->x_in[s]);
         return upload_field(c, X.data());
@@ -529,20 +537,21 @@ lbms_status lbms_get_fields(lbms_ctx* c, double* X, double* u, double* tau) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
     const int64_t S = c->L.S;
     const int nf = c->L.nf;
-    const size_t es = x_size(c->L.precision);
-    auto to_double = [&](const std::vector<unsigned char>& b, int64_t idx) {
-        return c->L.precision == LBMS_FP64 ? reinterpret_cast<const double*>(b.data())[idx]
-                                           : (double)reinterpret_cast<const float*>(b.data())[idx];
-    };
+    const int prec = c->L.precision;
     if (X) {
-        std::vector<unsigned char> b(3 * (size_t)S * es);
+        std::vector<unsigned char> b(3 * (size_t)S * x_size(prec));
         CK(cudaMemcpyAsync(b.data(), c->L.b.X[c->L.cur], b.size(), cudaMemcpyDeviceToHost, c->stream), "read X");
         CK(cudaStreamSynchronize(c->stream), "read X");
         c->d2h += b.size();
         std::fill(X, X + 3 * c->N, 0.0);
         for (int s = 0; s < 3; ++s)
-            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = c->L.xref[s] + to_double(b, s * S + i);
+            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = get_x(prec, b.data(), s * S + i);
     }
+    const size_t es = field_size(prec);
+    auto to_double = [&](const std::vector<unsigned char>& b, int64_t idx) {
+        return prec == LBMS_FP64 ? reinterpret_cast<const double*>(b.data())[idx]
+                                 : (double)reinterpret_cast<const float*>(b.data())[idx];
+    };
     if (u || tau) {
         if (!c->L.b.fields) {
             c->L.b.fields = dev_alloc(c, (size_t)(3 + 3 * c->dim) * S * es);

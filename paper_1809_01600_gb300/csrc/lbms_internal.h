@@ -14,15 +14,15 @@ constexpr int kRedBoundary = 1;        // slot of the boundary sums
 constexpr int kRedMaxBlocks = 1216;    // 152 SMs x 8 resident blocks of 256 threads
 
 struct DevBuffers {
-    void* f[2] = {nullptr, nullptr};   // post-collision populations minus w Xref, [3][Q][S]
-    void* X[2] = {nullptr, nullptr};   // mole fractions minus Xref, [3][S]
-    void* snap = nullptr;              // residual snapshot (minus Xref), [3][S]
+    void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]
+    void* X[2] = {nullptr, nullptr};   // mole fractions (double or double-float pairs), [3][S]
+    double* snap = nullptr;            // residual snapshot, [3][S]
     int* nbr = nullptr;                // [Q-1][S]
     int* rows = nullptr;               // [3][nrows]: x = 0, x = 1, x = nx-1 cell per row (-1 if solid)
     double* red_partials = nullptr;    // [kRedMaxBlocks][kRedSlots]
     unsigned int* red_counter = nullptr;  // one per slot
     double* red_out = nullptr;         // [2][kRedSlots]
-    void* fields = nullptr;            // [3 + 3 dim][S] of tau and u (lazy)
+    void* fields = nullptr;            // [3 + 3 dim][S] of tau and u (lazy), FP64 or FP32
 };
 
 struct Launch {
@@ -33,7 +33,6 @@ struct Launch {
     int nrows = 0;                     // ny * nz
     int cur = 0;                       // lattice holding the latest post-collision state
     DevBuffers b;
-    double xref[3] = {0, 0, 0};        // shift of the stored state
     double xin[3] = {0, 0, 0};
     double q[3] = {0, 0, 0};
     double D12 = 1, D13 = 1, D23 = 1;  // lattice binary diffusivities
@@ -45,6 +44,7 @@ struct Launch {
 
 size_t pop_size(int precision);    // bytes per stored population
 size_t x_size(int precision);      // bytes per stored mole fraction
+size_t field_size(int precision);  // bytes per tau / u value of the fields kernel
 int residual_blocks(const Launch& L);
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st);

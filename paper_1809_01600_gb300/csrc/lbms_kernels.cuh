@@ -1,17 +1,21 @@
 // Device side of the solver: the fused collide + stream + Maxwell-Stefan
 // step, the field recomputation, initialisation and the FP64 reductions.
 //
-// Storage (all compact over the fluid cells, x-fastest order, padded row
-// stride S, a multiple of 32 elements):
-//   f[s][k][i]   post-collision populations, two lattices (pull streaming),
-//                stored shifted: f - w_k Xref_s (Xref = a fixed reference
-//                composition), in FP64, FP32 or FP16 (FP16 scaled by 2^10)
-//   X[s][i]      mole fractions of a step minus Xref, two buffers (this step /
-//                previous), FP64 or FP32
-//   nbr[k-1][i]  fluid index of the source cell x - e_k, or an NB_* code
-// The shift is exact algebra (sum_k w_k = 1, w_k = w_opp(k)); it keeps the
-// stored numbers near zero so that their rounding error scales with the
-// departure from Xref rather than with X itself.
+// State (compact over the fluid cells, x-fastest order, padded row stride S,
+// a multiple of 32 elements), two copies for pull streaming:
+//   X[s][i]     mole fraction of species s after the step.  FP64, or a
+//               double-float pair (hi, lo) of FP32 words whose sum carries
+//               ~48 significant bits, so that per-step changes far below one
+//               FP32 ulp still accumulate (a plain FP32 state freezes about
+//               ulp / (slowest decay rate) away from the steady state).
+//   h[s][k][i]  non-equilibrium part of the post-collision population,
+//               h = f* - w_k X, in FP64, FP32 or FP16 (FP16 scaled by 2^14).
+//   nbr[k-1][i] fluid index of the source cell x - e_k, or an NB_* code.
+// A pulled population is f_k(x) = w_k X(src) + h_k(src).  The step works on
+// d_k = f_k(x) - w_k X_old(x) = w_k (X(src) - X_old(x)) + h_k(src): small
+// numbers whose exchange terms are exactly antisymmetric between two cells,
+// so streaming conserves every species without depending on how the weights
+// round.
 #pragma once
 
 #include <cstdint>
@@ -38,60 +42,75 @@ struct MsConst {
     int drift;            // 1: drift velocity carries the Maxwell-Stefan flux tau does not
 };
 
-// Population storage: P = T, or __half holding (f - w Xref) * 2^10.
-constexpr float kHalfScale = 1024.0f;
-constexpr float kHalfInvScale = 1.0f / 1024.0f;
+// ------------------------------------------------------------------ storage
+// Non-equilibrium populations: P = T, or __half holding h * 2^14.
+constexpr float kHalfScale = 16384.0f;
+constexpr float kHalfInvScale = 1.0f / 16384.0f;
 
 template <typename T, typename P>
 struct Pop {
     __device__ __forceinline__ static T load(const P* p) { return T(*p); }
-    __device__ __forceinline__ static void store(P* p, T v) { *p = P(v); }
+    __device__ __forceinline__ static P quant(T v) { return P(v); }
+    __device__ __forceinline__ static T dequant(P v) { return T(v); }
 };
 template <>
 struct Pop<float, __half> {
     __device__ __forceinline__ static float load(const __half* p) { return __half2float(*p) * kHalfInvScale; }
-    __device__ __forceinline__ static void store(__half* p, float v) { *p = __float2half_rn(v * kHalfScale); }
+    __device__ __forceinline__ static __half quant(float v) { return __float2half_rn(v * kHalfScale); }
+    __device__ __forceinline__ static float dequant(__half v) { return __half2float(v) * kHalfInvScale; }
 };
 
-template <typename T, typename P>
+// Mole fractions: double, or float2 = (hi, lo) double-float.
+template <typename XT>
+struct Xv;
+template <>
+struct Xv<double> {
+    using T = double;
+    double v;
+    __device__ __forceinline__ static Xv load(const double* p) { return Xv{*p}; }
+    __device__ __forceinline__ void store(double* p) const { *p = v; }
+    __device__ __forceinline__ T value() const { return v; }
+    __device__ __forceinline__ double to_double() const { return v; }
+    // a - b, accurate to the working precision of the difference
+    __device__ __forceinline__ static T diff(const Xv& a, const Xv& b) { return a.v - b.v; }
+    __device__ __forceinline__ Xv plus(T d) const { return Xv{v + d}; }
+};
+template <>
+struct Xv<float2> {
+    using T = float;
+    float hi, lo;
+    __device__ __forceinline__ static Xv load(const float2* p) {
+        const float2 q = *p;
+        return Xv{q.x, q.y};
+    }
+    __device__ __forceinline__ void store(float2* p) const { *p = make_float2(hi, lo); }
+    __device__ __forceinline__ T value() const { return hi + lo; }
+    __device__ __forceinline__ double to_double() const { return (double)hi + (double)lo; }
+    // hi parts of neighbouring values are close, so hi_a - hi_b is exact
+    __device__ __forceinline__ static T diff(const Xv& a, const Xv& b) { return (a.hi - b.hi) + (a.lo - b.lo); }
+    // (hi, lo) + d renormalised with Knuth's two-sum
+    __device__ __forceinline__ Xv plus(float d) const {
+        const float t = lo + d;
+        const float s = hi + t;
+        const float bb = s - hi;
+        const float e = (hi - (s - bb)) + (t - bb);
+        return Xv{s, e};
+    }
+};
+
+template <typename XT, typename P>
 struct StepParams {
-    const P* __restrict__ fin;
-    P* __restrict__ fout;
-    const T* __restrict__ xprev;
-    T* __restrict__ xnext;
+    const P* __restrict__ hin;
+    P* __restrict__ hout;
+    const XT* __restrict__ xin;
+    XT* __restrict__ xout;
     const int* __restrict__ nbr;
     int64_t S;
     int nf;
-    T xref[3];      // shift of the stored populations and mole fractions
-    T dxin[3];      // inlet mole fractions minus xref (Eq. 36)
-    T qout[3];      // outlet flux per node per step (Eq. 39)
-    MsConst<T> c;
+    XT xbc[3];                        // inlet mole fractions (Eq. 36), in the X format
+    typename Xv<XT>::T qout[3];       // outlet flux per node per step (Eq. 39)
+    MsConst<typename Xv<XT>::T> c;
 };
-
-// -------------------------------------------------------------------------
-// Lagged gradient (Eq. 35 read as a central difference on every axis): the
-// stored field of the previous step, a solid neighbour mirrored to the centre
-// value, one-sided at the inlet/outlet nodes.
-template <class L, typename T>
-__device__ __forceinline__ void lagged_gradient(const T* __restrict__ xprev, int64_t S, int i,
-                                                const int (&nb)[L::Q], T (&g)[3][L::DIM]) {
-    T xc[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) xc[s] = xprev[s * S + i];
-#pragma unroll
-    for (int d = 0; d < L::DIM; ++d) {
-        const int cp = nb[2 + 2 * d];  // source of -e_d is the cell at x + e_d
-        const int cm = nb[1 + 2 * d];  // source of +e_d is the cell at x - e_d
-        const bool hp = cp >= NB_SOLID;
-        const bool hm = cm >= NB_SOLID;
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const T pv = cp >= 0 ? xprev[s * S + cp] : xc[s];
-            const T mv = cm >= 0 ? xprev[s * S + cm] : xc[s];
-            g[s][d] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv - xc[s] : (hm ? xc[s] - mv : T(0)));
-        }
-    }
-}
 
 // -------------------------------------------------------------------------
 // Maxwell-Stefan coupling of one cell (lattice units, c_s^2 = 1/3):
@@ -168,10 +187,11 @@ __device__ __forceinline__ void ms_coupling(const T (&X)[3], const T (&g)[3][DIM
 // -------------------------------------------------------------------------
 // One time step for every fluid cell (one thread per cell):
 // pull-stream with bounce-back / inlet / outlet, moments, lagged gradient,
-// coupling, BGK collision, store post-collision populations and X.
-// All population arithmetic is on shifted values g_k = f_k - w_k Xref.
-template <class L, typename T, typename P>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams<T, P> p) {
+// Maxwell-Stefan coupling, BGK collision, store h and X.
+template <class L, typename XT, typename P>
+__global__ void __launch_bounds__(256) step_kernel(const StepParams<XT, P> p) {
+    using T = typename Xv<XT>::T;
+    using XV = Xv<XT>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -183,75 +203,102 @@ __global__ void __launch_bounds__(256) step_kernel(const StepParams<T, P> p) {
 #pragma unroll
     for (int k = 1; k < Q; ++k) nb[k] = __ldg(p.nbr + (int64_t)(k - 1) * S + i);
 
-    // 1. stream (pull) with the boundary rules
-    T f[3][Q];
     constexpr T wx = T(weight_xplus<L>());
+    T d[3][Q];      // f_k(x) - w_k X_old(x) after streaming
+    T g[3][DIM];    // lagged gradient (Eq. 35 as central differences)
+    XV xo[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
+        xo[s] = XV::load(p.xin + s * S + i);
+        T dxs[Q];   // X(src) - X_old(x) for fluid sources, 0 otherwise
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             const int src = nb[k];
-            const P* row = p.fin + (int64_t)(s * Q + k) * S;
-            const P* orow = p.fin + (int64_t)(s * Q + opp<L>(k)) * S;
-            T val;
-            if (src >= 0)
-                val = Pop<T, P>::load(row + src);
-            else if (src == NB_SOLID)
+            const P* row = p.hin + (int64_t)(s * Q + k) * S;
+            const P* orow = p.hin + (int64_t)(s * Q + opp<L>(k)) * S;
+            T val, dx = T(0);
+            if (k == 0) {
+                val = Pop<T, P>::load(row + i);
+            } else if (src >= 0) {
+                dx = XV::diff(XV::load(p.xin + s * S + src), xo[s]);
+                val = T(weight<L>(k)) * dx + Pop<T, P>::load(row + src);
+            } else if (src == NB_SOLID) {
                 val = Pop<T, P>::load(orow + i);
-            else if (src == NB_OUTLET)
+            } else if (src == NB_OUTLET) {
                 val = Pop<T, P>::load(orow + i) - (T(weight<L>(opp<L>(k))) / wx) * p.qout[s];
-            else
+            } else {
                 val = T(0);
-            f[s][k] = val;
+            }
+            d[s][k] = val;
+            dxs[k] = dx;
         }
+        // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
-                f[s][k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * p.dxin[s] - f[s][opp<L>(k)];
+            if (L::e(k, 0) == 1 && nb[k] == NB_INLET) {
+                const XV xb = XV::load(&p.xbc[s]);
+                d[s][k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * XV::diff(xb, xo[s]) - d[s][opp<L>(k)];
+            }
+        }
+        // lagged gradient from the neighbour differences already at hand
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int kp = 2 + 2 * a;   // source of -e_a: the cell at x + e_a
+            const int km = 1 + 2 * a;   // source of +e_a: the cell at x - e_a
+            const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
+            const T pv = dxs[kp], mv = dxs[km];   // relative to X_old(x); solid -> mirror (0)
+            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
         }
     }
 
-    // 2. moments (shifted: Xs = X - Xref)
-    T Xs[3], X[3];
+    // moments: dX = sum_k d_k, X = X_old + dX
+    T dX[3], X[3];
+    XV xn[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         T acc = T(0);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) acc += f[s][k];
-        Xs[s] = acc;
-        X[s] = p.xref[s] + acc;
+        for (int k = 0; k < Q; ++k) acc += d[s][k];
+        dX[s] = acc;
+        xn[s] = xo[s].plus(acc);
+        X[s] = xn[s].value();
     }
 
-    // 3-6. lagged gradient and Maxwell-Stefan coupling
-    T g[3][DIM];
-    lagged_gradient<L, T>(p.xprev, S, i, nb, g);
     T tau[3], v[3][DIM];
     ms_coupling<T, DIM>(X, g, p.c, tau, v, nullptr);
 
-    // 7. BGK collision towards w X (1 + e.v / c_s^2), shifted by w Xref, store
+    // BGK collision towards w X (1 + e.v / c_s^2); h* = f* - w X
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const T it = T(1) / tau[s];
+        const T keep = T(1) - it;
+        T rest = T(0);
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        for (int k = 1; k < Q; ++k) {
             T ev = T(0);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) ev += T(L::e(k, d)) * v[s][d];
+            for (int a = 0; a < DIM; ++a) ev += T(L::e(k, a)) * v[s][a];
             const T w = T(weight<L>(k));
-            const T geq = w * Xs[s] + T(3) * w * X[s] * ev;
-            Pop<T, P>::store(p.fout + (int64_t)(s * Q + k) * S + i, f[s][k] - (f[s][k] - geq) * it);
+            const T hk = (d[s][k] - w * dX[s]) * keep + T(3) * w * X[s] * ev * it;
+            const P q = Pop<T, P>::quant(hk);
+            rest -= Pop<T, P>::dequant(q);
+            p.hout[(int64_t)(s * Q + k) * S + i] = q;
         }
-        p.xnext[s * S + i] = Xs[s];
+        // the rest population closes sum_k h_k = 0 (mass) on the stored values
+        p.hout[(int64_t)(s * Q) * S + i] = Pop<T, P>::quant(rest);
+        xn[s].store(p.xout + s * S + i);
     }
 }
 
 // -------------------------------------------------------------------------
 // tau and the component velocity of the last step, recomputed from the
 // stored fields (X of the step and of the step before).
-template <class L, typename T>
-__global__ void fields_kernel(const T* __restrict__ xcur, const T* __restrict__ xprev,
-                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<T> c, T xr0, T xr1, T xr2,
-                              T* __restrict__ tau_out, T* __restrict__ u_out) {
+template <class L, typename XT>
+__global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict__ xprev,
+                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<typename Xv<XT>::T> c,
+                              typename Xv<XT>::T* __restrict__ tau_out, typename Xv<XT>::T* __restrict__ u_out) {
+    using T = typename Xv<XT>::T;
+    using XV = Xv<XT>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -260,36 +307,45 @@ __global__ void fields_kernel(const T* __restrict__ xcur, const T* __restrict__ 
     nb[0] = i;
 #pragma unroll
     for (int k = 1; k < Q; ++k) nb[k] = nbr[(int64_t)(k - 1) * S + i];
-    const T xr[3] = {xr0, xr1, xr2};
-    T X[3];
+    T X[3], g[3][DIM];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) X[s] = xr[s] + xcur[s * S + i];
-    T g[3][DIM];
-    lagged_gradient<L, T>(xprev, S, i, nb, g);
+    for (int s = 0; s < 3; ++s) {
+        X[s] = XV::load(xcur + s * S + i).value();
+        const XV xo = XV::load(xprev + s * S + i);
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int cp = nb[2 + 2 * a], cm = nb[1 + 2 * a];
+            const bool hp = cp >= NB_SOLID, hm = cm >= NB_SOLID;
+            const T pv = cp >= 0 ? XV::diff(XV::load(xprev + s * S + cp), xo) : T(0);
+            const T mv = cm >= 0 ? XV::diff(XV::load(xprev + s * S + cm), xo) : T(0);
+            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+        }
+    }
     T tau[3], v[3][DIM], u[3][DIM];
     ms_coupling<T, DIM>(X, g, c, tau, v, u);
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         tau_out[s * S + i] = tau[s];
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) u_out[(int64_t)(s * DIM + d) * S + i] = u[s][d];
+        for (int a = 0; a < DIM; ++a) u_out[(int64_t)(s * DIM + a) * S + i] = u[s][a];
     }
 }
 
-// f = w X (Eq. 29 equilibrium) in the current lattice, i.e. stored w (X - Xref);
-// both X buffers and the residual snapshot take X - Xref (already in x0).
-template <class L, typename T, typename P>
-__global__ void init_kernel(P* __restrict__ f, const T* __restrict__ x0, T* __restrict__ x1, T* __restrict__ snap,
-                            int64_t S, int nf) {
+// Equilibrium start (Eq. 29, f = w X): h = 0; the second X copy and the
+// residual snapshot take X (already in x0).
+template <class L, typename XT, typename P>
+__global__ void init_kernel(P* __restrict__ h, const XT* __restrict__ x0, XT* __restrict__ x1,
+                            double* __restrict__ snap, int64_t S, int nf) {
+    using T = typename Xv<XT>::T;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        const T Xs = x0[s * S + i];
-        x1[s * S + i] = Xs;
-        snap[s * S + i] = Xs;
+        const XT v = x0[s * S + i];
+        x1[s * S + i] = v;
+        snap[s * S + i] = Xv<XT>::load(&v).to_double();
 #pragma unroll
-        for (int k = 0; k < L::Q; ++k) Pop<T, P>::store(f + (int64_t)(s * L::Q + k) * S + i, T(weight<L>(k)) * Xs);
+        for (int k = 0; k < L::Q; ++k) h[(int64_t)(s * L::Q + k) * S + i] = Pop<T, P>::quant(T(0));
     }
 }
 
@@ -357,47 +413,44 @@ __device__ __forceinline__ void reduce_to_out(double (&acc)[NV], double* __restr
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Residual sums over fluid cells in FP64 (X = Xref + stored value):
-// out[0..2] = sum (X - snap)^2, out[3..5] = sum X^2, out[6..8] = sum X,
-// out[9] = count of non-finite X.  When update != 0 the snapshot takes X.
-// Grid-stride over a persistent grid.
-template <typename T>
-__global__ void __launch_bounds__(256) residual_kernel(const T* __restrict__ X, T* __restrict__ snap,
-                                                       int64_t S, int nf, int update, double xr0, double xr1,
-                                                       double xr2, double* __restrict__ partials,
+// Residual sums over fluid cells in FP64: out[0..2] = sum (X - snap)^2,
+// out[3..5] = sum X^2, out[6..8] = sum X, out[9] = count of non-finite X.
+// When update != 0 the snapshot takes X.  Grid-stride over a persistent grid.
+template <typename XT>
+__global__ void __launch_bounds__(256) residual_kernel(const XT* __restrict__ X, double* __restrict__ snap,
+                                                       int64_t S, int nf, int update, double* __restrict__ partials,
                                                        unsigned int* __restrict__ counter, double* __restrict__ out) {
-    const double xr[3] = {xr0, xr1, xr2};
     double acc[10];
 #pragma unroll
     for (int v = 0; v < 10; ++v) acc[v] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const double xs = (double)X[s * S + i];
-            const double d = xs - (double)snap[s * S + i];
-            const double x = xr[s] + xs;
+            const double x = Xv<XT>::load(X + s * S + i).to_double();
+            const double d = x - snap[s * S + i];
             acc[s] += d * d;
             acc[3 + s] += x * x;
             acc[6 + s] += x;
             if (!isfinite(x)) acc[9] += 1.0;
-            if (update) snap[s * S + i] = X[s * S + i];
+            if (update) snap[s * S + i] = x;
         }
     }
     reduce_to_out<10>(acc, partials, counter, out);
 }
 
 // Boundary sums in FP64 over the ny*nz rows: out[0..2] = net flux toward +x
-// through the plane between x = 0 and x = 1 (post-collision populations of
-// the last step), out[3..5] = sum of X over the outlet column.
-template <class L, typename T, typename P>
-__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ f, const T* __restrict__ X,
+// through the plane between x = 0 and x = 1, carried by the post-collision
+// populations w X + h of the last step; out[3..5] = sum of X over the outlet
+// column.
+template <class L, typename XT, typename P>
+__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, const XT* __restrict__ X,
                                                        const int* __restrict__ nbr, int64_t S,
                                                        const int* __restrict__ row_x0, const int* __restrict__ row_x1,
-                                                       const int* __restrict__ row_out, int nrows, double xr0,
-                                                       double xr1, double xr2, double* __restrict__ partials,
-                                                       unsigned int* __restrict__ counter, double* __restrict__ out) {
+                                                       const int* __restrict__ row_out, int nrows,
+                                                       double* __restrict__ partials, unsigned int* __restrict__ counter,
+                                                       double* __restrict__ out) {
+    using T = typename Xv<XT>::T;
     constexpr int Q = L::Q;
-    const double xr[3] = {xr0, xr1, xr2};
     double acc[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) acc[v] = 0.0;
@@ -414,19 +467,21 @@ __global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ f, 
                 if (nbr[(int64_t)(opp<L>(k) - 1) * S + i0] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
-                        acc[s] += (double)Pop<T, P>::load(f + (int64_t)(s * Q + k) * S + i0) + w * xr[s];
+                        acc[s] += w * Xv<XT>::load(X + s * S + i0).to_double() +
+                                  (double)Pop<T, P>::load(h + (int64_t)(s * Q + k) * S + i0);
                 }
             } else if (ex == -1 && i1 >= 0) {
                 if (nbr[(int64_t)(opp<L>(k) - 1) * S + i1] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
-                        acc[s] -= (double)Pop<T, P>::load(f + (int64_t)(s * Q + k) * S + i1) + w * xr[s];
+                        acc[s] -= w * Xv<XT>::load(X + s * S + i1).to_double() +
+                                  (double)Pop<T, P>::load(h + (int64_t)(s * Q + k) * S + i1);
                 }
             }
         }
         if (io >= 0) {
 #pragma unroll
-            for (int s = 0; s < 3; ++s) acc[3 + s] += xr[s] + (double)X[s * S + io];
+            for (int s = 0; s < 3; ++s) acc[3 + s] += Xv<XT>::load(X + s * S + io).to_double();
         }
     }
     reduce_to_out<6>(acc, partials, counter, out);

@@ -1,5 +1,7 @@
-// Kernel instantiations and launch wrappers (D2Q9 / D3Q19 x FP64 / FP32 /
-// FP16-stored populations with FP32 arithmetic).
+// Kernel instantiations and launch wrappers: D2Q9 / D3Q19 x
+//   FP64   (X double,           h double)
+//   FP32   (X double-float pair, h float)
+//   FP16   (X double-float pair, h half, FP32 arithmetic)
 #include <algorithm>
 
 #include "lbms_internal.h"
@@ -37,70 +39,76 @@ MsConst<T> make_const(const Launch& L) {
     return c;
 }
 
-template <class Lat, typename T, typename P>
+inline void to_x(double v, double& out) { out = v; }
+inline void to_x(double v, float2& out) {
+    const float hi = (float)v;
+    out = make_float2(hi, (float)(v - (double)hi));
+}
+
+template <class Lat, typename XT, typename P>
 cudaError_t step_t(const Launch& L, cudaStream_t st) {
-    StepParams<T, P> p;
-    p.fin = static_cast<const P*>(L.b.f[L.cur]);
-    p.fout = static_cast<P*>(L.b.f[L.cur ^ 1]);
-    p.xprev = static_cast<const T*>(L.b.X[L.cur]);
-    p.xnext = static_cast<T*>(L.b.X[L.cur ^ 1]);
+    using T = typename Xv<XT>::T;
+    StepParams<XT, P> p;
+    p.hin = static_cast<const P*>(L.b.f[L.cur]);
+    p.hout = static_cast<P*>(L.b.f[L.cur ^ 1]);
+    p.xin = static_cast<const XT*>(L.b.X[L.cur]);
+    p.xout = static_cast<XT*>(L.b.X[L.cur ^ 1]);
     p.nbr = L.b.nbr;
     p.S = L.S;
     p.nf = L.nf;
     for (int s = 0; s < 3; ++s) {
-        p.xref[s] = T(L.xref[s]);
-        p.dxin[s] = T(L.xin[s] - L.xref[s]);
+        to_x(L.xin[s], p.xbc[s]);
         p.qout[s] = T(L.q[s]);
     }
     p.c = make_const<T>(L);
     const int grid = (L.nf + kBlock - 1) / kBlock;
-    step_kernel<Lat, T, P><<<grid, kBlock, 0, st>>>(p);
+    step_kernel<Lat, XT, P><<<grid, kBlock, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T, typename P>
+template <class Lat, typename XT, typename P>
 cudaError_t init_t(const Launch& L, cudaStream_t st) {
     const int grid = (L.nf + kBlock - 1) / kBlock;
-    init_kernel<Lat, T, P><<<grid, kBlock, 0, st>>>(static_cast<P*>(L.b.f[L.cur]), static_cast<const T*>(L.b.X[L.cur]),
-                                                    static_cast<T*>(L.b.X[L.cur ^ 1]), static_cast<T*>(L.b.snap), L.S,
-                                                    L.nf);
+    init_kernel<Lat, XT, P><<<grid, kBlock, 0, st>>>(static_cast<P*>(L.b.f[L.cur]),
+                                                     static_cast<const XT*>(L.b.X[L.cur]),
+                                                     static_cast<XT*>(L.b.X[L.cur ^ 1]), L.b.snap, L.S, L.nf);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T, typename P>
+template <class Lat, typename XT, typename P>
 cudaError_t fields_t(const Launch& L, cudaStream_t st) {
+    using T = typename Xv<XT>::T;
     const int grid = (L.nf + kBlock - 1) / kBlock;
     T* base = static_cast<T*>(L.b.fields);
-    fields_kernel<Lat, T><<<grid, kBlock, 0, st>>>(static_cast<const T*>(L.b.X[L.cur]),
-                                                   static_cast<const T*>(L.b.X[L.cur ^ 1]), L.b.nbr, L.S, L.nf,
-                                                   make_const<T>(L), T(L.xref[0]), T(L.xref[1]), T(L.xref[2]), base,
-                                                   base + 3 * L.S);
+    fields_kernel<Lat, XT><<<grid, kBlock, 0, st>>>(static_cast<const XT*>(L.b.X[L.cur]),
+                                                    static_cast<const XT*>(L.b.X[L.cur ^ 1]), L.b.nbr, L.S, L.nf,
+                                                    make_const<T>(L), base, base + 3 * L.S);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename XT>
 cudaError_t residual_t(const Launch& L, int update, cudaStream_t st) {
-    residual_kernel<T><<<residual_blocks(L), kBlock, 0, st>>>(
-        static_cast<const T*>(L.b.X[L.cur]), static_cast<T*>(L.b.snap), L.S, L.nf, update, L.xref[0], L.xref[1],
-        L.xref[2], L.b.red_partials, L.b.red_counter + kRedResidual, L.b.red_out + kRedResidual * kRedSlots);
+    residual_kernel<XT><<<residual_blocks(L), kBlock, 0, st>>>(
+        static_cast<const XT*>(L.b.X[L.cur]), L.b.snap, L.S, L.nf, update, L.b.red_partials,
+        L.b.red_counter + kRedResidual, L.b.red_out + kRedResidual * kRedSlots);
     return cudaGetLastError();
 }
 
-template <class Lat, typename T, typename P>
+template <class Lat, typename XT, typename P>
 cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
     const int blocks = std::max(1, std::min((L.nrows + kBlock - 1) / kBlock, kRedMaxBlocks / 2));
-    boundary_kernel<Lat, T, P><<<blocks, kBlock, 0, st>>>(
-        static_cast<const P*>(L.b.f[L.cur]), static_cast<const T*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
-        L.b.rows + L.nrows, L.b.rows + 2 * L.nrows, L.nrows, L.xref[0], L.xref[1], L.xref[2],
-        L.b.red_partials + kRedMaxBlocks * kRedSlots / 2, L.b.red_counter + kRedBoundary,
-        L.b.red_out + kRedBoundary * kRedSlots);
+    boundary_kernel<Lat, XT, P><<<blocks, kBlock, 0, st>>>(
+        static_cast<const P*>(L.b.f[L.cur]), static_cast<const XT*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
+        L.b.rows + L.nrows, L.b.rows + 2 * L.nrows, L.nrows, L.b.red_partials + kRedMaxBlocks * kRedSlots / 2,
+        L.b.red_counter + kRedBoundary, L.b.red_out + kRedBoundary * kRedSlots);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t pop_size(int precision) { return precision == 0 ? sizeof(double) : (precision == 1 ? sizeof(float) : 2); }
-size_t x_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
+size_t x_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float2); }
+size_t field_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
 
 int residual_blocks(const Launch& L) {
     const int want = (L.nf + kBlock - 1) / kBlock;
@@ -111,12 +119,12 @@ int residual_blocks(const Launch& L) {
     do {                                                                                    \
         if (L.dim == 2) {                                                                   \
             if (L.precision == 0) return FN<D2Q9, double, double>(__VA_ARGS__);             \
-            if (L.precision == 1) return FN<D2Q9, float, float>(__VA_ARGS__);               \
-            return FN<D2Q9, float, __half>(__VA_ARGS__);                                    \
+            if (L.precision == 1) return FN<D2Q9, float2, float>(__VA_ARGS__);              \
+            return FN<D2Q9, float2, __half>(__VA_ARGS__);                                   \
         }                                                                                   \
         if (L.precision == 0) return FN<D3Q19, double, double>(__VA_ARGS__);                \
-        if (L.precision == 1) return FN<D3Q19, float, float>(__VA_ARGS__);                  \
-        return FN<D3Q19, float, __half>(__VA_ARGS__);                                       \
+        if (L.precision == 1) return FN<D3Q19, float2, float>(__VA_ARGS__);                 \
+        return FN<D3Q19, float2, __half>(__VA_ARGS__);                                      \
     } while (0)
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(step_t, L, st); }
@@ -125,7 +133,7 @@ cudaError_t launch_fields(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(fiel
 cudaError_t launch_boundary(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(boundary_t, L, st); }
 
 cudaError_t launch_residual(const Launch& L, int update, cudaStream_t st) {
-    return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float>(L, update, st);
+    return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float2>(L, update, st);
 }
 
 }  // namespace lbms
