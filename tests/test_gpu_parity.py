@@ -235,7 +235,9 @@ def test_steady_state_single_and_half_precision(lbms, precision, xtol):
     case = cases.porous((12, 20), radius=2, porosity=0.6, seed=7, current_A_cm2=1.0)
     s = lbms.Solver.from_case(case, precision=precision)
     s.set_bc(case.x_in, case.current_A_cm2)
-    n, r, st = s.run_to_residual(1e-10, 400000, raise_on_fail=False)
+    tol = 1e-10 if precision == "fp32" else 1e-8
+    n, r, st = s.run_to_residual(tol, 400000, raise_on_fail=False)
+    s.step(20000)      # well past the tolerance: the state stays put
     o = Oracle(case)
     o.run_to_residual(1e-12, 400000, 100)
     X = s.fields()
@@ -243,9 +245,8 @@ def test_steady_state_single_and_half_precision(lbms, precision, xtol):
     err = np.abs(X - o.X)[:, f].max()
     eta, _ = s.overpotential()
     assert eta == pytest.approx(o.overpotential(), rel=1e-4)
-    if xtol is not None:
-        assert st == lbms.LBMS_OK and r <= 1e-10
-        assert err <= xtol
+    assert st == lbms.LBMS_OK and r <= tol
+    assert err <= xtol
 
 
 def test_lattice_constants_match_oracle(lbms):
@@ -289,7 +290,7 @@ def test_full_size_fp32_closed_box_conservation(lbms):
     assert np.allclose(tot, tot0, rtol=1e-9)
 
 
-@pytest.mark.parametrize("precision,rtol", [("fp32", 1e-11), ("fp16", 1e-8)])
+@pytest.mark.parametrize("precision,rtol", [("fp32", 1e-11), ("fp16", 1e-7)])
 def test_closed_box_conservation_low_precision(lbms, precision, rtol):
     """Streaming exchanges w_k (X(src) - X(x)) + h_k terms that cancel
     exactly between cells, and the rest population closes sum_k h_k = 0 on
