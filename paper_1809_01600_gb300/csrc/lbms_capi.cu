@@ -157,11 +157,13 @@ lbms_status compute_props(lbms_ctx* c, const lbms_species* sp, const lbms_diffus
     return LBMS_OK;
 }
 
-// Fluid list (x-fastest) and the pull-neighbour table nbr[k-1][i].
+// Pull-neighbour table: row i holds, for k = 1..Q-1, the fluid index of the
+// source x - e_k or an NB_* code, padded to nb_width ints.
 template <class Lat>
 void build_neighbours(const lbms_ctx* c, const std::vector<int>& index_of, int64_t S, std::vector<int>& nbr) {
     const int nf = (int)c->fluid_cell.size();
-    nbr.assign((size_t)(Lat::Q - 1) * S, NB_SOLID);
+    constexpr int NW = nb_width<Lat>();
+    nbr.assign((size_t)NW * S, NB_SOLID);
     for (int i = 0; i < nf; ++i) {
         const int64_t cell = c->fluid_cell[i];
         const int x = (int)(cell % c->nx);
@@ -181,7 +183,7 @@ void build_neighbours(const lbms_ctx* c, const std::vector<int>& index_of, int64
                 const int j = index_of[((int64_t)sz * c->ny + sy) * c->nx + sx];
                 code = j >= 0 ? j : NB_SOLID;
             }
-            nbr[(size_t)(k - 1) * S + i] = code;
+            nbr[(size_t)i * NW + (k - 1)] = code;
         }
     }
 }
@@ -432,7 +434,8 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     }
     const size_t sbytes = (size_t)3 * L.S * sizeof(double);
     L.b.snap = static_cast<double*>(dev_alloc(c, sbytes));
-    L.b.nbr = static_cast<int*>(dev_alloc(c, (size_t)(c->Q - 1) * L.S * sizeof(int)));
+    const int nbw = c->dim == 2 ? nb_width<D2Q9>() : nb_width<D3Q19>();
+    L.b.nbr = static_cast<int*>(dev_alloc(c, (size_t)nbw * L.S * sizeof(int)));
     L.b.rows = static_cast<int*>(dev_alloc(c, 3 * (size_t)nrows * sizeof(int)));
     L.b.red_partials = static_cast<double*>(dev_alloc(c, (size_t)kRedMaxBlocks * kRedSlots * sizeof(double)));
     L.b.red_counter = static_cast<unsigned int*>(dev_alloc(c, 4 * sizeof(unsigned int)));

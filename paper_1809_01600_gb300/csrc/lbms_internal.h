@@ -17,7 +17,7 @@ struct DevBuffers {
     void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]
     void* X[2] = {nullptr, nullptr};   // mole fractions (double or double-float pairs), [3][S]
     double* snap = nullptr;            // residual snapshot, [3][S]
-    int* nbr = nullptr;                // [Q-1][S]
+    int* nbr = nullptr;                // [S][nb_width]
     int* rows = nullptr;               // [3][nrows]: x = 0, x = 1, x = nx-1 cell per row (-1 if solid)
     double* red_partials = nullptr;    // [kRedMaxBlocks][kRedSlots]
     unsigned int* red_counter = nullptr;  // one per slot

@@ -10,7 +10,8 @@
 //               ulp / (slowest decay rate) away from the steady state).
 //   h[s][k][i]  non-equilibrium part of the post-collision population,
 //               h = f* - w_k X, in FP64, FP32 or FP16 (FP16 scaled by 2^14).
-//   nbr[k-1][i] fluid index of the source cell x - e_k, or an NB_* code.
+//   nbr[i][k-1] fluid index of the source cell x - e_k, or an NB_* code;
+//               one row of nb_width() ints per cell, read with 16-byte loads.
 // A pulled population is f_k(x) = w_k X(src) + h_k(src).  The step works on
 // d_k = f_k(x) - w_k X_old(x) = w_k (X(src) - X_old(x)) + h_k(src): small
 // numbers whose exchange terms are exactly antisymmetric between two cells,
@@ -41,6 +42,21 @@ struct MsConst {
     T tau_min, tau_max;
     int drift;            // 1: drift velocity carries the Maxwell-Stefan flux tau does not
 };
+
+// Neighbour row of cell i: nb[k] for k = 1..Q-1 (nb[0] is left to the caller).
+template <class L>
+__device__ __forceinline__ void load_neighbours(const int* __restrict__ nbr, int i, int (&nb)[L::Q]) {
+    constexpr int NW = nb_width<L>();
+    const int4* row = reinterpret_cast<const int4*>(nbr + (int64_t)i * NW);
+#pragma unroll
+    for (int j = 0; j < NW / 4; ++j) {
+        const int4 v = __ldg(row + j);
+        if (1 + 4 * j + 0 < L::Q) nb[1 + 4 * j + 0] = v.x;
+        if (1 + 4 * j + 1 < L::Q) nb[1 + 4 * j + 1] = v.y;
+        if (1 + 4 * j + 2 < L::Q) nb[1 + 4 * j + 2] = v.z;
+        if (1 + 4 * j + 3 < L::Q) nb[1 + 4 * j + 3] = v.w;
+    }
+}
 
 // ------------------------------------------------------------------ storage
 // Non-equilibrium populations: P = T, or __half holding h * 2^14.
@@ -185,109 +201,119 @@ __device__ __forceinline__ void ms_coupling(const T (&X)[3], const T (&g)[3][DIM
 }
 
 // -------------------------------------------------------------------------
-// One time step for every fluid cell (one thread per cell):
-// pull-stream with bounce-back / inlet / outlet, moments, lagged gradient,
-// Maxwell-Stefan coupling, BGK collision, store h and X.
-template <class L, typename XT, typename P>
-__global__ void __launch_bounds__(256) step_kernel(const StepParams<XT, P> p) {
+// One time step for every fluid cell: pull-stream with bounce-back / inlet /
+// outlet, moments, lagged gradient, Maxwell-Stefan coupling, BGK collision,
+// store h and X.
+//
+// Thread mapping: a block covers W consecutive fluid cells with 3 W threads,
+// one per (species, cell); warps are species-uniform, so every load and store
+// of a warp walks consecutive cells of one species row.  The three threads of
+// a cell meet once, through shared memory, to exchange X and its gradient for
+// the coupling (which needs all species).
+template <class L, typename XT, typename P, int W>
+__global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P> p) {
     using T = typename Xv<XT>::T;
     using XV = Xv<XT>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= p.nf) return;
+    __shared__ T sX[3][W];
+    __shared__ T sG[3][DIM][W];
+
+    const int s = threadIdx.x / W;          // species of this thread
+    const int c = threadIdx.x - s * W;      // cell slot in the block
+    const int i = blockIdx.x * W + c;
+    const bool active = i < p.nf;
     const int64_t S = p.S;
+    const P* hs = p.hin + (int64_t)s * Q * S;
 
     int nb[Q];
-    nb[0] = i;
+    T d[Q];          // f_k(x) - w_k X_old(x) after streaming
+    XV xo, xn;
+    T dX = T(0);
+    if (active) {
+        nb[0] = i;
+        load_neighbours<L>(p.nbr, i, nb);
+        xo = XV::load(p.xin + s * S + i);
+        T dxs[Q];    // X(src) - X_old(x) for fluid sources, 0 otherwise
+        constexpr T wx = T(weight_xplus<L>());
+        const T qs = s == 0 ? p.qout[0] : (s == 1 ? p.qout[1] : p.qout[2]);
+        const XT* xrow = p.xin + s * S;
+        d[0] = Pop<T, P>::load(hs + i);
+        dxs[0] = T(0);
+        // Every link loads unconditionally (no branch between the gathers): a
+        // fluid source gives h_k(src) and X(src); otherwise the cell's own
+        // h_opp(k) (bounce-back and outlet) and its own X, whose difference is 0.
 #pragma unroll
-    for (int k = 1; k < Q; ++k) nb[k] = __ldg(p.nbr + (int64_t)(k - 1) * S + i);
-
-    constexpr T wx = T(weight_xplus<L>());
-    T d[3][Q];      // f_k(x) - w_k X_old(x) after streaming
-    T g[3][DIM];    // lagged gradient (Eq. 35 as central differences)
-    XV xo[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        xo[s] = XV::load(p.xin + s * S + i);
-        T dxs[Q];   // X(src) - X_old(x) for fluid sources, 0 otherwise
-#pragma unroll
-        for (int k = 0; k < Q; ++k) {
+        for (int k = 1; k < Q; ++k) {
             const int src = nb[k];
-            const P* row = p.hin + (int64_t)(s * Q + k) * S;
-            const P* orow = p.hin + (int64_t)(s * Q + opp<L>(k)) * S;
-            T val, dx = T(0);
-            if (k == 0) {
-                val = Pop<T, P>::load(row + i);
-            } else if (src >= 0) {
-                dx = XV::diff(XV::load(p.xin + s * S + src), xo[s]);
-                val = T(weight<L>(k)) * dx + Pop<T, P>::load(row + src);
-            } else if (src == NB_SOLID) {
-                val = Pop<T, P>::load(orow + i);
-            } else if (src == NB_OUTLET) {
-                val = Pop<T, P>::load(orow + i) - (T(weight<L>(opp<L>(k))) / wx) * p.qout[s];
-            } else {
-                val = T(0);
-            }
-            d[s][k] = val;
+            const bool fluid = src >= 0;
+            const P* hp = fluid ? hs + (int64_t)k * S + src : hs + (int64_t)opp<L>(k) * S + i;
+            const T hv = Pop<T, P>::load(hp);
+            const T dx = XV::diff(XV::load(xrow + (fluid ? src : i)), xo);
+            T val = T(weight<L>(k)) * dx + hv;
+            if (src == NB_OUTLET) val -= (T(weight<L>(opp<L>(k))) / wx) * qs;
+            d[k] = val;
             dxs[k] = dx;
         }
         // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
+        const XT xb_raw = s == 0 ? p.xbc[0] : (s == 1 ? p.xbc[1] : p.xbc[2]);
+        const XV xb = XV::load(&xb_raw);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            if (L::e(k, 0) == 1 && nb[k] == NB_INLET) {
-                const XV xb = XV::load(&p.xbc[s]);
-                d[s][k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * XV::diff(xb, xo[s]) - d[s][opp<L>(k)];
-            }
+            if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
+                d[k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * XV::diff(xb, xo) - d[opp<L>(k)];
         }
-        // lagged gradient from the neighbour differences already at hand
+        // lagged gradient (Eq. 35 as central differences) from the differences at hand
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const int kp = 2 + 2 * a;   // source of -e_a: the cell at x + e_a
             const int km = 1 + 2 * a;   // source of +e_a: the cell at x - e_a
             const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
-            const T pv = dxs[kp], mv = dxs[km];   // relative to X_old(x); solid -> mirror (0)
-            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+            const T pv = dxs[kp], mv = dxs[km];   // solid neighbour -> mirror (0)
+            sG[s][a][c] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
         }
-    }
-
-    // moments: dX = sum_k d_k, X = X_old + dX
-    T dX[3], X[3];
-    XV xn[3];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) acc += d[s][k];
-        dX[s] = acc;
-        xn[s] = xo[s].plus(acc);
-        X[s] = xn[s].value();
+        for (int k = 0; k < Q; ++k) dX += d[k];
+        xn = xo.plus(dX);
+        sX[s][c] = xn.value();
     }
+    __syncthreads();
+    if (!active) return;
 
+    T X[3], g[3][DIM];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        X[r] = sX[r][c];
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) g[r][a] = sG[r][a][c];
+    }
     T tau[3], v[3][DIM];
     ms_coupling<T, DIM>(X, g, p.c, tau, v, nullptr);
+    const T ts = s == 0 ? tau[0] : (s == 1 ? tau[1] : tau[2]);
+    const T Xs = X[s == 0 ? 0 : (s == 1 ? 1 : 2)];
+    T vs[DIM];
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) vs[a] = s == 0 ? v[0][a] : (s == 1 ? v[1][a] : v[2][a]);
 
     // BGK collision towards w X (1 + e.v / c_s^2); h* = f* - w X
+    const T it = T(1) / ts;
+    const T keep = T(1) - it;
+    P* ho = p.hout + (int64_t)s * Q * S;
+    T rest = T(0);
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        const T it = T(1) / tau[s];
-        const T keep = T(1) - it;
-        T rest = T(0);
+    for (int k = 1; k < Q; ++k) {
+        T ev = T(0);
 #pragma unroll
-        for (int k = 1; k < Q; ++k) {
-            T ev = T(0);
-#pragma unroll
-            for (int a = 0; a < DIM; ++a) ev += T(L::e(k, a)) * v[s][a];
-            const T w = T(weight<L>(k));
-            const T hk = (d[s][k] - w * dX[s]) * keep + T(3) * w * X[s] * ev * it;
-            const P q = Pop<T, P>::quant(hk);
-            rest -= Pop<T, P>::dequant(q);
-            p.hout[(int64_t)(s * Q + k) * S + i] = q;
-        }
-        // the rest population closes sum_k h_k = 0 (mass) on the stored values
-        p.hout[(int64_t)(s * Q) * S + i] = Pop<T, P>::quant(rest);
-        xn[s].store(p.xout + s * S + i);
+        for (int a = 0; a < DIM; ++a) ev += T(L::e(k, a)) * vs[a];
+        const T w = T(weight<L>(k));
+        const T hk = (d[k] - w * dX) * keep + T(3) * w * Xs * ev * it;
+        const P q = Pop<T, P>::quant(hk);
+        rest -= Pop<T, P>::dequant(q);
+        ho[(int64_t)k * S + i] = q;
     }
+    // the rest population closes sum_k h_k = 0 (mass) on the stored values
+    ho[i] = Pop<T, P>::quant(rest);
+    xn.store(p.xout + s * S + i);
 }
 
 // -------------------------------------------------------------------------
@@ -306,7 +332,7 @@ __global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict_
     int nb[Q];
     nb[0] = i;
 #pragma unroll
-    for (int k = 1; k < Q; ++k) nb[k] = nbr[(int64_t)(k - 1) * S + i];
+    load_neighbours<L>(nbr, i, nb);
     T X[3], g[3][DIM];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
@@ -464,14 +490,14 @@ __global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, 
             const double w = weight<L>(k);
             if (ex == 1 && i0 >= 0) {
                 // f*_k at x = 0 reaches x + e_k when that cell (the source of opp(k)) is fluid
-                if (nbr[(int64_t)(opp<L>(k) - 1) * S + i0] >= 0) {
+                if (nbr[(int64_t)i0 * nb_width<L>() + opp<L>(k) - 1] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
                         acc[s] += w * Xv<XT>::load(X + s * S + i0).to_double() +
                                   (double)Pop<T, P>::load(h + (int64_t)(s * Q + k) * S + i0);
                 }
             } else if (ex == -1 && i1 >= 0) {
-                if (nbr[(int64_t)(opp<L>(k) - 1) * S + i1] >= 0) {
+                if (nbr[(int64_t)i1 * nb_width<L>() + opp<L>(k) - 1] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
                         acc[s] -= w * Xv<XT>::load(X + s * S + i1).to_double() +

@@ -63,6 +63,13 @@ __host__ __device__ constexpr double weight_xplus() {
     return s;
 }
 
+// Width (ints) of one cell's row of the neighbour table: the Q-1 links,
+// padded to a multiple of 4 so that a row is read with 16-byte loads.
+template <class L>
+__host__ __device__ constexpr int nb_width() {
+    return ((L::Q - 1) + 3) / 4 * 4;
+}
+
 // Neighbour-table codes for a link whose source x - e_k is not a fluid cell.
 enum : int {
     NB_SOLID = -1,   // half-way bounce-back

@@ -12,6 +12,7 @@ namespace lbms {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kCells = 32;     // cells per block of the step kernel (3 threads per cell)
 
 template <typename T>
 MsConst<T> make_const(const Launch& L) {
@@ -61,8 +62,8 @@ cudaError_t step_t(const Launch& L, cudaStream_t st) {
         p.qout[s] = T(L.q[s]);
     }
     p.c = make_const<T>(L);
-    const int grid = (L.nf + kBlock - 1) / kBlock;
-    step_kernel<Lat, XT, P><<<grid, kBlock, 0, st>>>(p);
+    const int grid = (L.nf + kCells - 1) / kCells;
+    step_kernel<Lat, XT, P, kCells><<<grid, 3 * kCells, 0, st>>>(p);
     return cudaGetLastError();
 }
 
