@@ -180,6 +180,32 @@ lbms_status lbms_get_info(const lbms_ctx *ctx, lbms_info *info);
 /* Waits for all queued work of the handle. */
 lbms_status lbms_synchronize(lbms_ctx *ctx);
 
+/* Allocation-free residual sums, for callers that cannot allocate device
+ * memory: code inside a CUDA graph being captured, hosts whose memory pool
+ * owns every device allocation, loops that must not call cudaMalloc (it
+ * synchronises the device).  The paper has no counterpart; this is an
+ * integration helper that runs the residual reduction of lbms_residual on
+ * caller-owned FP64 fields.
+ *   X, snapshot  device, 3*n doubles each, species-major ([species][cell]);
+ *                1 <= n <= INT32_MAX (larger n: LBMS_EINVAL).
+ *   update       nonzero: the snapshot takes X after the sums are read.
+ *   out          device, 10 doubles: out[0..2] = sum (X - snapshot)^2 per
+ *                species, out[3..5] = sum X^2, out[6..8] = sum X,
+ *                out[9] = number of non-finite X.  The residual of
+ *                lbms_residual is max_i sqrt(out[i]) / (K sqrt(out[3+i])).
+ *   stream       cudaStream_t (NULL = legacy default); the call only queues
+ *                work and does not synchronise.
+ * Scratch: a fixed 40 KiB device array (512 blocks x 10 partial sums) plus a
+ * counter, held by every GPU that loads this library until the process
+ * exits; the grid is capped at 512 blocks, so any n in range fits.  The first
+ * call on a device looks up the scratch address (once per device, with that
+ * device current): make that first call before any stream capture.  All calls
+ * share the scratch, so calls that overlap on the GPU (other streams, other
+ * threads) race; serialise them.  Nothing is allocated or freed.
+ * LBMS_EINVAL on NULL pointers or n out of range, LBMS_ECUDA on a CUDA error. */
+lbms_status lbms_residual_sums_noalloc(const double *X, double *snapshot, int64_t n, int update,
+                                       double *out, void *stream);
+
 void lbms_destroy(lbms_ctx *ctx);
 const char *lbms_last_error(const lbms_ctx *ctx);
 const char *lbms_status_string(lbms_status s);

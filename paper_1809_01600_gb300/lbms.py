@@ -27,7 +27,7 @@ STATUS_NAMES = {0: "LBMS_OK", 1: "LBMS_EINVAL", 2: "LBMS_ENOMEM", 3: "LBMS_ECUDA
 EXPORTS = ("lbms_default_options", "lbms_create", "lbms_set_bc", "lbms_set_fields", "lbms_step",
            "lbms_residual", "lbms_run_to_residual", "lbms_get_fields", "lbms_overpotential",
            "lbms_boundary_flux", "lbms_get_info", "lbms_synchronize", "lbms_destroy",
-           "lbms_last_error", "lbms_status_string")
+           "lbms_last_error", "lbms_status_string", "lbms_residual_sums_noalloc")
 
 
 class LbmsError(RuntimeError):
@@ -106,6 +106,7 @@ def load(build_if_needed: bool = True):
         "lbms_destroy": (None, [P]),
         "lbms_last_error": (C.c_char_p, [P]),
         "lbms_status_string": (C.c_char_p, [C.c_int]),
+        "lbms_residual_sums_noalloc": (st, [P, P, I64, C.c_int, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
