@@ -409,6 +409,8 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     L.nf = (int)c->fluid_cell.size();
     L.S = ((int64_t)L.nf + 31) / 32 * 32;
     L.nrows = nrows;
+    if ((int64_t)c->Q * L.S >= (int64_t)std::numeric_limits<int>::max())
+        return bail(fail(c, LBMS_EINVAL, "too many fluid cells: Q x cells must stay below 2^31"));
     L.D12 = c->gas.D_lat[0][1];
     L.D13 = c->gas.D_lat[0][2];
     L.D23 = c->gas.D_lat[1][2];

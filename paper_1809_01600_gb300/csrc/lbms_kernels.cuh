@@ -129,74 +129,89 @@ struct StepParams {
 };
 
 // -------------------------------------------------------------------------
-// Maxwell-Stefan coupling of one cell (lattice units, c_s^2 = 1/3):
+// Maxwell-Stefan coupling of one cell (lattice units, c_s^2 = 1/3), for one
+// species s at a time (the step kernel runs one thread per species):
 //  B (Eq. 32, species 3 = reference n), J_1,2 = -B^-1 g (Eqs. 31, 33, 34,
 //  Gamma = I), J_3 from the n-th row of Eq. 19; D_i from Eq. 24 with the
 //  flux ratios of the electrode reaction (nu_j / nu_i), the mixture value
 //  for the inert species; tau_i from Eq. 25 clamped; and the drift velocity
 //  (velocity slot of Eq. 26) that makes the carried flux the Maxwell-Stefan
-//  flux J_i.
+//  flux J_i.  FP32 divisions use the fast hardware reciprocal (2 ulp).
+template <typename T>
+struct Arith {
+    __device__ __forceinline__ static T div(T a, T b) { return a / b; }
+};
+template <>
+struct Arith<float> {
+    __device__ __forceinline__ static float div(float a, float b) { return __fdividef(a, b); }
+};
+
 template <typename T, int DIM>
-__device__ __forceinline__ void ms_coupling(const T (&X)[3], const T (&g)[3][DIM], const MsConst<T>& c,
-                                            T (&tau)[3], T (&v)[3][DIM], T (*u)[DIM]) {
+__device__ __forceinline__ void ms_flux(const T (&X)[3], const T (&g)[3][DIM], const MsConst<T>& c, int s,
+                                        T (&J)[DIM]) {
     const T B11 = X[0] * c.i13 + X[1] * c.i12 + X[2] * c.i13;
     const T B12 = -X[0] * (c.i12 - c.i13);
     const T B21 = -X[1] * (c.i12 - c.i23);
     const T B22 = X[1] * c.i23 + X[0] * c.i12 + X[2] * c.i23;
     const T det = B11 * B22 - B12 * B21;
-    const T idet = det > T(0) ? T(1) / det : T(0);
-    const T d3 = X[0] * c.i13 + X[1] * c.i23;
-    const T id3 = d3 > T(0) ? T(1) / d3 : T(0);
-
-    T J[3][DIM];
+    const T idet = det > T(0) ? Arith<T>::div(T(1), det) : T(0);
+    if (s == 0) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        J[0][d] = -(B22 * g[0][d] - B12 * g[1][d]) * idet;
-        J[1][d] = -(B11 * g[1][d] - B21 * g[0][d]) * idet;
-        J[2][d] = (-g[2][d] + X[2] * (J[0][d] * c.i13 + J[1][d] * c.i23)) * id3;
+        for (int d = 0; d < DIM; ++d) J[d] = -(B22 * g[0][d] - B12 * g[1][d]) * idet;
+    } else if (s == 1) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) J[d] = -(B11 * g[1][d] - B21 * g[0][d]) * idet;
+    } else {
+        const T d3 = X[0] * c.i13 + X[1] * c.i23;
+        const T id3 = d3 > T(0) ? Arith<T>::div(T(1), d3) : T(0);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const T j1 = -(B22 * g[0][d] - B12 * g[1][d]) * idet;
+            const T j2 = -(B11 * g[1][d] - B21 * g[0][d]) * idet;
+            J[d] = (-g[2][d] + X[2] * (j1 * c.i13 + j2 * c.i23)) * id3;
+        }
     }
+}
 
-    const T md = T(kMixDelta);
-    const T ex2 = T(kEpsX * kEpsX);
+// tau_s (Eqs. 24-25) and the drift velocity v_s of species s; also returns
+// X_s / (X_s^2 + eps^2), the guarded 1/X_s used by the component velocity.
+template <typename T, int DIM>
+__device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], const T (&J)[DIM], const MsConst<T>& c,
+                                         int s, T& tau, T (&v)[DIM], T& xinv) {
+    const T Xs = s == 0 ? X[0] : (s == 1 ? X[1] : X[2]);
+    T D;
+    if (c.reacting[s]) {
+        const T inv = c.a[s][0] * X[0] + c.a[s][1] * X[1] + c.a[s][2] * X[2];
+        D = inv > T(0) ? Arith<T>::div(T(1), inv) : T(kDBig);
+    } else {
+        // mixture value sum_{j!=s} X_j / sum_{j!=s} X_j / D_sj
+        const T md = T(kMixDelta);
+        const T num = (s == 0 ? X[1] + X[2] : (s == 1 ? X[0] + X[2] : X[0] + X[1])) + md;
+        const T den = (s == 0 ? X[1] * c.i12 + X[2] * c.i13
+                              : (s == 1 ? X[0] * c.i12 + X[2] * c.i23 : X[0] * c.i13 + X[1] * c.i23)) +
+                      md * c.h[s];
+        D = Arith<T>::div(num, den);
+    }
+    T t = D * T(3) + T(0.5);
+    t = t < c.tau_min ? c.tau_min : (t > c.tau_max ? c.tau_max : t);
+    tau = t;
+    const T Dt = (t - T(0.5)) * T(1.0 / 3.0);
+    xinv = Arith<T>::div(Xs, Xs * Xs + T(kEpsX * kEpsX));
+    if (c.drift) {
+        T vn2 = T(0);
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        T D;
-        if (c.reacting[s]) {
-            const T inv = c.a[s][0] * X[0] + c.a[s][1] * X[1] + c.a[s][2] * X[2];
-            D = inv > T(0) ? T(1) / inv : T(kDBig);
-        } else {
-            // mixture value sum_{j!=s} X_j / sum_{j!=s} X_j / D_sj
-            const T num = (X[0] + X[1] + X[2] - X[s]) + md;
-            const T den = (s == 0 ? X[1] * c.i12 + X[2] * c.i13
-                                  : (s == 1 ? X[0] * c.i12 + X[2] * c.i23 : X[0] * c.i13 + X[1] * c.i23)) +
-                          md * c.h[s];
-            D = num / den;
+        for (int d = 0; d < DIM; ++d) {
+            v[d] = (J[d] + Dt * gs[d]) * xinv;
+            vn2 += v[d] * v[d];
         }
-        T t = D * T(3) + T(0.5);
-        t = t < c.tau_min ? c.tau_min : (t > c.tau_max ? c.tau_max : t);
-        tau[s] = t;
-        const T Dt = (t - T(0.5)) * T(1.0 / 3.0);
-        const T xinv = X[s] / (X[s] * X[s] + ex2);
-        if (c.drift) {
-            T vn2 = T(0);
+        if (vn2 > T(kVMax * kVMax)) {
+            const T sc = T(kVMax) / sqrt(vn2);
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) {
-                v[s][d] = (J[s][d] + Dt * g[s][d]) * xinv;
-                vn2 += v[s][d] * v[s][d];
-            }
-            if (vn2 > T(kVMax * kVMax)) {
-                const T sc = T(kVMax) / sqrt(vn2);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) v[s][d] *= sc;
-            }
-        } else {
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) v[s][d] = T(0);
+            for (int d = 0; d < DIM; ++d) v[d] *= sc;
         }
-        if (u) {
+    } else {
 #pragma unroll
-            for (int d = 0; d < DIM; ++d) u[s][d] = J[s][d] * xinv;
-        }
+        for (int d = 0; d < DIM; ++d) v[d] = T(0);
     }
 }
 
@@ -211,7 +226,7 @@ __device__ __forceinline__ void ms_coupling(const T (&X)[3], const T (&g)[3][DIM
 // a cell meet once, through shared memory, to exchange X and its gradient for
 // the coupling (which needs all species).
 template <class L, typename XT, typename P, int W>
-__global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P> p) {
+__global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XT, P> p) {
     using T = typename Xv<XT>::T;
     using XV = Xv<XT>;
     constexpr int Q = L::Q;
@@ -224,6 +239,7 @@ __global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P>
     const int i = blockIdx.x * W + c;
     const bool active = i < p.nf;
     const int64_t S = p.S;
+    const int S32 = (int)S;      // Q * S < 2^31 (checked at create): 32-bit offsets in a species block
     const P* hs = p.hin + (int64_t)s * Q * S;
 
     int nb[Q];
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P>
         for (int k = 1; k < Q; ++k) {
             const int src = nb[k];
             const bool fluid = src >= 0;
-            const P* hp = fluid ? hs + (int64_t)k * S + src : hs + (int64_t)opp<L>(k) * S + i;
+            const P* hp = hs + (fluid ? k * S32 + src : opp<L>(k) * S32 + i);
             const T hv = Pop<T, P>::load(hp);
             const T dx = XV::diff(XV::load(xrow + (fluid ? src : i)), xo);
             T val = T(weight<L>(k)) * dx + hv;
@@ -287,16 +303,15 @@ __global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P>
 #pragma unroll
         for (int a = 0; a < DIM; ++a) g[r][a] = sG[r][a][c];
     }
-    T tau[3], v[3][DIM];
-    ms_coupling<T, DIM>(X, g, p.c, tau, v, nullptr);
-    const T ts = s == 0 ? tau[0] : (s == 1 ? tau[1] : tau[2]);
-    const T Xs = X[s == 0 ? 0 : (s == 1 ? 1 : 2)];
-    T vs[DIM];
+    T gs[DIM], J[DIM], vs[DIM], ts, xinv;
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) vs[a] = s == 0 ? v[0][a] : (s == 1 ? v[1][a] : v[2][a]);
+    for (int a = 0; a < DIM; ++a) gs[a] = s == 0 ? g[0][a] : (s == 1 ? g[1][a] : g[2][a]);
+    ms_flux<T, DIM>(X, g, p.c, s, J);
+    ms_relax<T, DIM>(X, gs, J, p.c, s, ts, vs, xinv);
+    const T Xs = s == 0 ? X[0] : (s == 1 ? X[1] : X[2]);
 
     // BGK collision towards w X (1 + e.v / c_s^2); h* = f* - w X
-    const T it = T(1) / ts;
+    const T it = Arith<T>::div(T(1), ts);
     const T keep = T(1) - it;
     P* ho = p.hout + (int64_t)s * Q * S;
     T rest = T(0);
@@ -309,7 +324,7 @@ __global__ void __launch_bounds__(3 * W, 10) step_kernel(const StepParams<XT, P>
         const T hk = (d[k] - w * dX) * keep + T(3) * w * Xs * ev * it;
         const P q = Pop<T, P>::quant(hk);
         rest -= Pop<T, P>::dequant(q);
-        ho[(int64_t)k * S + i] = q;
+        ho[k * S32 + i] = q;
     }
     // the rest population closes sum_k h_k = 0 (mass) on the stored values
     ho[i] = Pop<T, P>::quant(rest);
@@ -347,13 +362,16 @@ __global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict_
             g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
         }
     }
-    T tau[3], v[3][DIM], u[3][DIM];
-    ms_coupling<T, DIM>(X, g, c, tau, v, u);
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        tau_out[s * S + i] = tau[s];
+        T J[DIM], v[DIM], gs[DIM], tau, xinv;
 #pragma unroll
-        for (int a = 0; a < DIM; ++a) u_out[(int64_t)(s * DIM + a) * S + i] = u[s][a];
+        for (int a = 0; a < DIM; ++a) gs[a] = g[s][a];
+        ms_flux<T, DIM>(X, g, c, s, J);
+        ms_relax<T, DIM>(X, gs, J, c, s, tau, v, xinv);
+        tau_out[s * S + i] = tau;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) u_out[(int64_t)(s * DIM + a) * S + i] = J[a] * xinv;
     }
 }
 
