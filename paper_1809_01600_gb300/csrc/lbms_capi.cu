@@ -207,20 +207,21 @@ void apply_bc(lbms_ctx* c) {
         for (int s = 0; s < 3; ++s) c->L.q[s] = 0.0;
 }
 
-// Mole fractions in the device format: double, or a double-float pair.
-void put_x(int precision, unsigned char* buf, int64_t idx, double v) {
+// Mole fractions in the device format: double, or a double-float pair whose
+// hi word is at [s][i] and lo word at [3 + s][i] (idx = s * S + i).
+void put_x(int precision, unsigned char* buf, int64_t S, int64_t idx, double v) {
     if (precision == LBMS_FP64) {
         reinterpret_cast<double*>(buf)[idx] = v;
     } else {
         const float hi = (float)v;
-        reinterpret_cast<float*>(buf)[2 * idx] = hi;
-        reinterpret_cast<float*>(buf)[2 * idx + 1] = (float)(v - (double)hi);
+        reinterpret_cast<float*>(buf)[idx] = hi;
+        reinterpret_cast<float*>(buf)[idx + 3 * S] = (float)(v - (double)hi);
     }
 }
 
-double get_x(int precision, const unsigned char* buf, int64_t idx) {
+double get_x(int precision, const unsigned char* buf, int64_t S, int64_t idx) {
     if (precision == LBMS_FP64) return reinterpret_cast<const double*>(buf)[idx];
-    return (double)reinterpret_cast<const float*>(buf)[2 * idx] + (double)reinterpret_cast<const float*>(buf)[2 * idx + 1];
+    return (double)reinterpret_cast<const float*>(buf)[idx] + (double)reinterpret_cast<const float*>(buf)[idx + 3 * S];
 }
 
 // Copies a dense host field (3*N doubles) into X[cur] and restarts from the
@@ -230,7 +231,7 @@ lbms_status upload_field(lbms_ctx* c, const double* X) {
     const int nf = c->L.nf;
     std::vector<unsigned char> buf(3 * (size_t)S * x_size(c->L.precision), 0);
     for (int s = 0; s < 3; ++s)
-        for (int i = 0; i < nf; ++i) put_x(c->L.precision, buf.data(), s * S + i, X[(size_t)s * c->N + c->fluid_cell[i]]);
+        for (int i = 0; i < nf; ++i) put_x(c->L.precision, buf.data(), S, s * S + i, X[(size_t)s * c->N + c->fluid_cell[i]]);
     CK(cudaMemcpyAsync(c->L.b.X[c->L.cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream),
        "upload mole fractions");
     c->h2d += buf.size();
@@ -550,7 +551,7 @@ lbms_status lbms_get_fields(lbms_ctx* c, double* X, double* u, double* tau) {
         c->d2h += b.size();
         std::fill(X, X + 3 * c->N, 0.0);
         for (int s = 0; s < 3; ++s)
-            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = get_x(prec, b.data(), s * S + i);
+            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = get_x(prec, b.data(), S, s * S + i);
     }
     const size_t es = field_size(prec);
     auto to_double = [&](const std::vector<unsigned char>& b, int64_t idx) {

@@ -4,19 +4,23 @@
 // State (compact over the fluid cells, x-fastest order, padded row stride S,
 // a multiple of 32 elements), two copies for pull streaming:
 //   X[s][i]     mole fraction of species s after the step.  FP64, or a
-//               double-float pair (hi, lo) of FP32 words whose sum carries
-//               ~48 significant bits, so that per-step changes far below one
-//               FP32 ulp still accumulate (a plain FP32 state freezes about
-//               ulp / (slowest decay rate) away from the steady state).
+//               double-float pair of FP32 words, hi in X[s][i] and lo in
+//               X[3+s][i], whose sum carries ~48 significant bits, so that
+//               per-step changes far below one FP32 ulp still accumulate (a
+//               plain FP32 state freezes about ulp / (slowest decay rate)
+//               away from the steady state).
 //   h[s][k][i]  non-equilibrium part of the post-collision population,
 //               h = f* - w_k X, in FP64, FP32 or FP16 (FP16 scaled by 2^14).
 //   nbr[i][k-1] fluid index of the source cell x - e_k, or an NB_* code;
 //               one row of nb_width() ints per cell, read with 16-byte loads.
 // A pulled population is f_k(x) = w_k X(src) + h_k(src).  The step works on
-// d_k = f_k(x) - w_k X_old(x) = w_k (X(src) - X_old(x)) + h_k(src): small
-// numbers whose exchange terms are exactly antisymmetric between two cells,
-// so streaming conserves every species without depending on how the weights
-// round.
+// d_k = f_k(x) - w_k X_old(x) ~ w_k (X(src) - X_old(x)) + h_k(src): small
+// numbers whose exchange terms w_k (X(src) - X(x)) are exactly antisymmetric
+// between two cells, so streaming conserves every species without depending
+// on how the weights round.  With the pair format the exchange terms use the
+// hi words only (hi_src - hi_x is exact and antisymmetric); the lo word
+// enters the cell's own accumulation, so the steady state is resolved to one
+// FP32 ulp of X instead of freezing ulp / (decay rate) away from it.
 #pragma once
 
 #include <cstdint>
@@ -76,34 +80,37 @@ struct Pop<float, __half> {
     __device__ __forceinline__ static float dequant(__half v) { return __half2float(v) * kHalfInvScale; }
 };
 
-// Mole fractions: double, or float2 = (hi, lo) double-float.
-template <typename XT>
+// Mole fractions.  Xv<double>: one FP64 value.  Xv<float>: a double-float
+// pair whose hi word sits at X[s][i] and lo word at X[3+s][i].
+template <typename XS>
 struct Xv;
 template <>
 struct Xv<double> {
     using T = double;
     double v;
-    __device__ __forceinline__ static Xv load(const double* p) { return Xv{*p}; }
-    __device__ __forceinline__ void store(double* p) const { *p = v; }
+    __device__ __forceinline__ static Xv own(const double* xb, int64_t S, int s, int i) { return Xv{xb[s * S + i]}; }
+    // value of a neighbour as used by the exchange terms and the gradient
+    __device__ __forceinline__ static T nb(const double* xb, int64_t S, int s, int j) { return xb[s * S + j]; }
+    __device__ __forceinline__ T exch(T n) const { return n - v; }          // neighbour minus own
+    __device__ __forceinline__ T minus(const Xv& b) const { return v - b.v; }  // full precision
     __device__ __forceinline__ T value() const { return v; }
     __device__ __forceinline__ double to_double() const { return v; }
-    // a - b, accurate to the working precision of the difference
-    __device__ __forceinline__ static T diff(const Xv& a, const Xv& b) { return a.v - b.v; }
     __device__ __forceinline__ Xv plus(T d) const { return Xv{v + d}; }
+    __device__ __forceinline__ void store(double* xb, int64_t S, int s, int i) const { xb[s * S + i] = v; }
 };
 template <>
-struct Xv<float2> {
+struct Xv<float> {
     using T = float;
     float hi, lo;
-    __device__ __forceinline__ static Xv load(const float2* p) {
-        const float2 q = *p;
-        return Xv{q.x, q.y};
+    __device__ __forceinline__ static Xv own(const float* xb, int64_t S, int s, int i) {
+        return Xv{xb[s * S + i], xb[(3 + s) * S + i]};
     }
-    __device__ __forceinline__ void store(float2* p) const { *p = make_float2(hi, lo); }
+    __device__ __forceinline__ static T nb(const float* xb, int64_t S, int s, int j) { return xb[s * S + j]; }
+    // hi_n - hi is exact for neighbouring values and antisymmetric between two cells
+    __device__ __forceinline__ T exch(T n) const { return n - hi; }
+    __device__ __forceinline__ T minus(const Xv& b) const { return (hi - b.hi) + (lo - b.lo); }
     __device__ __forceinline__ T value() const { return hi + lo; }
     __device__ __forceinline__ double to_double() const { return (double)hi + (double)lo; }
-    // hi parts of neighbouring values are close, so hi_a - hi_b is exact
-    __device__ __forceinline__ static T diff(const Xv& a, const Xv& b) { return (a.hi - b.hi) + (a.lo - b.lo); }
     // (hi, lo) + d renormalised with Knuth's two-sum
     __device__ __forceinline__ Xv plus(float d) const {
         const float t = lo + d;
@@ -112,20 +119,24 @@ struct Xv<float2> {
         const float e = (hi - (s - bb)) + (t - bb);
         return Xv{s, e};
     }
+    __device__ __forceinline__ void store(float* xb, int64_t S, int s, int i) const {
+        xb[s * S + i] = hi;
+        xb[(3 + s) * S + i] = lo;
+    }
 };
 
-template <typename XT, typename P>
+template <typename XS, typename P>
 struct StepParams {
     const P* __restrict__ hin;
     P* __restrict__ hout;
-    const XT* __restrict__ xin;
-    XT* __restrict__ xout;
+    const XS* __restrict__ xin;
+    XS* __restrict__ xout;
     const int* __restrict__ nbr;
     int64_t S;
     int nf;
-    XT xbc[3];                        // inlet mole fractions (Eq. 36), in the X format
-    typename Xv<XT>::T qout[3];       // outlet flux per node per step (Eq. 39)
-    MsConst<typename Xv<XT>::T> c;
+    Xv<XS> xbc[3];                    // inlet mole fractions (Eq. 36), in the X format
+    typename Xv<XS>::T qout[3];       // outlet flux per node per step (Eq. 39)
+    MsConst<typename Xv<XS>::T> c;
 };
 
 // -------------------------------------------------------------------------
@@ -225,10 +236,10 @@ __device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], co
 // of a warp walks consecutive cells of one species row.  The three threads of
 // a cell meet once, through shared memory, to exchange X and its gradient for
 // the coupling (which needs all species).
-template <class L, typename XT, typename P, int W>
-__global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XT, P> p) {
-    using T = typename Xv<XT>::T;
-    using XV = Xv<XT>;
+template <class L, typename XS, typename P, int W>
+__global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> p) {
+    using T = typename Xv<XS>::T;
+    using XV = Xv<XS>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     __shared__ T sX[3][W];
@@ -249,11 +260,10 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XT, P> 
     if (active) {
         nb[0] = i;
         load_neighbours<L>(p.nbr, i, nb);
-        xo = XV::load(p.xin + s * S + i);
+        xo = XV::own(p.xin, S, s, i);
         T dxs[Q];    // X(src) - X_old(x) for fluid sources, 0 otherwise
         constexpr T wx = T(weight_xplus<L>());
         const T qs = s == 0 ? p.qout[0] : (s == 1 ? p.qout[1] : p.qout[2]);
-        const XT* xrow = p.xin + s * S;
         d[0] = Pop<T, P>::load(hs + i);
         dxs[0] = T(0);
         // Every link loads unconditionally (no branch between the gathers): a
@@ -265,19 +275,18 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XT, P> 
             const bool fluid = src >= 0;
             const P* hp = hs + (fluid ? k * S32 + src : opp<L>(k) * S32 + i);
             const T hv = Pop<T, P>::load(hp);
-            const T dx = XV::diff(XV::load(xrow + (fluid ? src : i)), xo);
+            const T dx = xo.exch(XV::nb(p.xin, S, s, fluid ? src : i));
             T val = T(weight<L>(k)) * dx + hv;
             if (src == NB_OUTLET) val -= (T(weight<L>(opp<L>(k))) / wx) * qs;
             d[k] = val;
             dxs[k] = dx;
         }
         // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
-        const XT xb_raw = s == 0 ? p.xbc[0] : (s == 1 ? p.xbc[1] : p.xbc[2]);
-        const XV xb = XV::load(&xb_raw);
+        const XV xb = s == 0 ? p.xbc[0] : (s == 1 ? p.xbc[1] : p.xbc[2]);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
-                d[k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * XV::diff(xb, xo) - d[opp<L>(k)];
+                d[k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * xb.minus(xo) - d[opp<L>(k)];
         }
         // lagged gradient (Eq. 35 as central differences) from the differences at hand
 #pragma unroll
@@ -328,18 +337,18 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XT, P> 
     }
     // the rest population closes sum_k h_k = 0 (mass) on the stored values
     ho[i] = Pop<T, P>::quant(rest);
-    xn.store(p.xout + s * S + i);
+    xn.store(p.xout, S, s, i);
 }
 
 // -------------------------------------------------------------------------
 // tau and the component velocity of the last step, recomputed from the
 // stored fields (X of the step and of the step before).
-template <class L, typename XT>
-__global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict__ xprev,
-                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<typename Xv<XT>::T> c,
-                              typename Xv<XT>::T* __restrict__ tau_out, typename Xv<XT>::T* __restrict__ u_out) {
-    using T = typename Xv<XT>::T;
-    using XV = Xv<XT>;
+template <class L, typename XS>
+__global__ void fields_kernel(const XS* __restrict__ xcur, const XS* __restrict__ xprev,
+                              const int* __restrict__ nbr, int64_t S, int nf, MsConst<typename Xv<XS>::T> c,
+                              typename Xv<XS>::T* __restrict__ tau_out, typename Xv<XS>::T* __restrict__ u_out) {
+    using T = typename Xv<XS>::T;
+    using XV = Xv<XS>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -351,14 +360,14 @@ __global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict_
     T X[3], g[3][DIM];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        X[s] = XV::load(xcur + s * S + i).value();
-        const XV xo = XV::load(xprev + s * S + i);
+        X[s] = XV::own(xcur, S, s, i).value();
+        const XV xo = XV::own(xprev, S, s, i);
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const int cp = nb[2 + 2 * a], cm = nb[1 + 2 * a];
             const bool hp = cp >= NB_SOLID, hm = cm >= NB_SOLID;
-            const T pv = cp >= 0 ? XV::diff(XV::load(xprev + s * S + cp), xo) : T(0);
-            const T mv = cm >= 0 ? XV::diff(XV::load(xprev + s * S + cm), xo) : T(0);
+            const T pv = cp >= 0 ? xo.exch(XV::nb(xprev, S, s, cp)) : T(0);
+            const T mv = cm >= 0 ? xo.exch(XV::nb(xprev, S, s, cm)) : T(0);
             g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
         }
     }
@@ -377,17 +386,17 @@ __global__ void fields_kernel(const XT* __restrict__ xcur, const XT* __restrict_
 
 // Equilibrium start (Eq. 29, f = w X): h = 0; the second X copy and the
 // residual snapshot take X (already in x0).
-template <class L, typename XT, typename P>
-__global__ void init_kernel(P* __restrict__ h, const XT* __restrict__ x0, XT* __restrict__ x1,
+template <class L, typename XS, typename P>
+__global__ void init_kernel(P* __restrict__ h, const XS* __restrict__ x0, XS* __restrict__ x1,
                             double* __restrict__ snap, int64_t S, int nf) {
-    using T = typename Xv<XT>::T;
+    using T = typename Xv<XS>::T;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        const XT v = x0[s * S + i];
-        x1[s * S + i] = v;
-        snap[s * S + i] = Xv<XT>::load(&v).to_double();
+        const Xv<XS> v = Xv<XS>::own(x0, S, s, i);
+        v.store(x1, S, s, i);
+        snap[s * S + i] = v.to_double();
 #pragma unroll
         for (int k = 0; k < L::Q; ++k) h[(int64_t)(s * L::Q + k) * S + i] = Pop<T, P>::quant(T(0));
     }
@@ -460,8 +469,8 @@ __device__ __forceinline__ void reduce_to_out(double (&acc)[NV], double* __restr
 // Residual sums over fluid cells in FP64: out[0..2] = sum (X - snap)^2,
 // out[3..5] = sum X^2, out[6..8] = sum X, out[9] = count of non-finite X.
 // When update != 0 the snapshot takes X.  Grid-stride over a persistent grid.
-template <typename XT>
-__global__ void __launch_bounds__(256) residual_kernel(const XT* __restrict__ X, double* __restrict__ snap,
+template <typename XS>
+__global__ void __launch_bounds__(256) residual_kernel(const XS* __restrict__ X, double* __restrict__ snap,
                                                        int64_t S, int nf, int update, double* __restrict__ partials,
                                                        unsigned int* __restrict__ counter, double* __restrict__ out) {
     double acc[10];
@@ -470,7 +479,7 @@ __global__ void __launch_bounds__(256) residual_kernel(const XT* __restrict__ X,
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const double x = Xv<XT>::load(X + s * S + i).to_double();
+            const double x = Xv<XS>::own(X, S, s, i).to_double();
             const double d = x - snap[s * S + i];
             acc[s] += d * d;
             acc[3 + s] += x * x;
@@ -486,14 +495,14 @@ __global__ void __launch_bounds__(256) residual_kernel(const XT* __restrict__ X,
 // through the plane between x = 0 and x = 1, carried by the post-collision
 // populations w X + h of the last step; out[3..5] = sum of X over the outlet
 // column.
-template <class L, typename XT, typename P>
-__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, const XT* __restrict__ X,
+template <class L, typename XS, typename P>
+__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, const XS* __restrict__ X,
                                                        const int* __restrict__ nbr, int64_t S,
                                                        const int* __restrict__ row_x0, const int* __restrict__ row_x1,
                                                        const int* __restrict__ row_out, int nrows,
                                                        double* __restrict__ partials, unsigned int* __restrict__ counter,
                                                        double* __restrict__ out) {
-    using T = typename Xv<XT>::T;
+    using T = typename Xv<XS>::T;
     constexpr int Q = L::Q;
     double acc[6];
 #pragma unroll
@@ -511,21 +520,21 @@ __global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, 
                 if (nbr[(int64_t)i0 * nb_width<L>() + opp<L>(k) - 1] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
-                        acc[s] += w * Xv<XT>::load(X + s * S + i0).to_double() +
+                        acc[s] += w * Xv<XS>::own(X, S, s, i0).to_double() +
                                   (double)Pop<T, P>::load(h + (int64_t)(s * Q + k) * S + i0);
                 }
             } else if (ex == -1 && i1 >= 0) {
                 if (nbr[(int64_t)i1 * nb_width<L>() + opp<L>(k) - 1] >= 0) {
 #pragma unroll
                     for (int s = 0; s < 3; ++s)
-                        acc[s] -= w * Xv<XT>::load(X + s * S + i1).to_double() +
+                        acc[s] -= w * Xv<XS>::own(X, S, s, i1).to_double() +
                                   (double)Pop<T, P>::load(h + (int64_t)(s * Q + k) * S + i1);
                 }
             }
         }
         if (io >= 0) {
 #pragma unroll
-            for (int s = 0; s < 3; ++s) acc[3 + s] += Xv<XT>::load(X + s * S + io).to_double();
+            for (int s = 0; s < 3; ++s) acc[3 + s] += Xv<XS>::own(X, S, s, io).to_double();
         }
     }
     reduce_to_out<6>(acc, partials, counter, out);

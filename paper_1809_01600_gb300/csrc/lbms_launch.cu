@@ -1,7 +1,7 @@
 // Kernel instantiations and launch wrappers: D2Q9 / D3Q19 x
 //   FP64   (X double,           h double)
-//   FP32   (X double-float pair, h float)
-//   FP16   (X double-float pair, h half, FP32 arithmetic)
+//   FP32   (X double-float pair in FP32 words, h float)
+//   FP16   (X double-float pair in FP32 words, h half, FP32 arithmetic)
 #include <algorithm>
 
 #include "lbms_internal.h"
@@ -40,10 +40,10 @@ MsConst<T> make_const(const Launch& L) {
     return c;
 }
 
-inline void to_x(double v, double& out) { out = v; }
-inline void to_x(double v, float2& out) {
-    const float hi = (float)v;
-    out = make_float2(hi, (float)(v - (double)hi));
+inline void to_x(double v, Xv<double>& out) { out.v = v; }
+inline void to_x(double v, Xv<float>& out) {
+    out.hi = (float)v;
+    out.lo = (float)(v - (double)out.hi);
 }
 
 template <class Lat, typename XT, typename P>
@@ -108,7 +108,7 @@ cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
 }  // namespace
 
 size_t pop_size(int precision) { return precision == 0 ? sizeof(double) : (precision == 1 ? sizeof(float) : 2); }
-size_t x_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float2); }
+size_t x_size(int precision) { return precision == 0 ? sizeof(double) : 2 * sizeof(float); }
 size_t field_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
 
 int residual_blocks(const Launch& L) {
@@ -120,12 +120,12 @@ int residual_blocks(const Launch& L) {
     do {                                                                                    \
         if (L.dim == 2) {                                                                   \
             if (L.precision == 0) return FN<D2Q9, double, double>(__VA_ARGS__);             \
-            if (L.precision == 1) return FN<D2Q9, float2, float>(__VA_ARGS__);              \
-            return FN<D2Q9, float2, __half>(__VA_ARGS__);                                   \
+            if (L.precision == 1) return FN<D2Q9, float, float>(__VA_ARGS__);              \
+            return FN<D2Q9, float, __half>(__VA_ARGS__);                                   \
         }                                                                                   \
         if (L.precision == 0) return FN<D3Q19, double, double>(__VA_ARGS__);                \
-        if (L.precision == 1) return FN<D3Q19, float2, float>(__VA_ARGS__);                 \
-        return FN<D3Q19, float2, __half>(__VA_ARGS__);                                      \
+        if (L.precision == 1) return FN<D3Q19, float, float>(__VA_ARGS__);                 \
+        return FN<D3Q19, float, __half>(__VA_ARGS__);                                      \
     } while (0)
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(step_t, L, st); }
@@ -134,7 +134,7 @@ cudaError_t launch_fields(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(fiel
 cudaError_t launch_boundary(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(boundary_t, L, st); }
 
 cudaError_t launch_residual(const Launch& L, int update, cudaStream_t st) {
-    return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float2>(L, update, st);
+    return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float>(L, update, st);
 }
 
 }  // namespace lbms

@@ -235,7 +235,9 @@ def test_steady_state_single_and_half_precision(lbms, precision, xtol):
     case = cases.porous((12, 20), radius=2, porosity=0.6, seed=7, current_A_cm2=1.0)
     s = lbms.Solver.from_case(case, precision=precision)
     s.set_bc(case.x_in, case.current_A_cm2)
-    tol = 1e-10 if precision == "fp32" else 1e-8
+    # the FP32 pair state jitters by about one FP32 ulp at steady state
+    # (residual floor ~1e-10 at K = 100); FP16 storage by more
+    tol = 1e-9 if precision == "fp32" else 1e-8
     n, r, st = s.run_to_residual(tol, 400000, raise_on_fail=False)
     s.step(20000)      # well past the tolerance: the state stays put
     o = Oracle(case)
