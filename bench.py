@@ -254,7 +254,7 @@ def main():
     per_launch = t_dev / args.steps
     achieved = nf * bpc / per_launch / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = ncu_traffic(args.workload, args.precision)
+    traffic = ncu_traffic(case.name, args.precision)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
