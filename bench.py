@@ -32,6 +32,7 @@ import numpy as np  # noqa: E402
 WORKLOADS = {
     "anode3d_256x128x128": "anode_3d_256x128x128",
     "anode2d_96x48": "anode_2d_96x48",
+    "sweep": None,
 }
 METRIC = "MLUPS/species"
 
@@ -49,6 +50,10 @@ def parse():
     ap.add_argument("--time-to-residual", type=float, default=0.0,
                     help="also run to this residual from the uniform start and report the time")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
+    ap.add_argument("--sweep-2d", type=int, default=8, help="2-D microstructures of the sweep")
+    ap.add_argument("--sweep-3d", type=int, default=8, help="3-D microstructures of the sweep")
+    ap.add_argument("--sweep-scale", type=float, default=1.0, help="size factor of the sweep grids")
+    ap.add_argument("--sweep-points", type=int, default=8, help="operating points per microstructure")
     return ap.parse_args()
 
 
@@ -201,6 +206,8 @@ def main():
     ws, rank, local = dist_env()
     if args.impl == "reference":
         return main_reference(args, ws, rank)
+    if args.workload == "sweep":
+        return main_sweep(args, ws, rank, local)
 
     import torch
     if not torch.cuda.is_available():
@@ -219,6 +226,7 @@ def main():
     s = L.Solver.from_case(case, precision=args.precision)
     s.set_bc(case.x_in, case.current_A_cm2)
     stream = torch.cuda.current_stream()
+    tinfo = s.info()
 
     # warm-up: W steps, then one graph-sized batch so the step graph exists
     s.step(args.warmup)
@@ -321,10 +329,128 @@ def main():
                            "porosity": round(case.porosity, 4), "current_A_cm2": case.current_A_cm2,
                            "x_in": list(case.x_in), "precision": args.precision,
                            "parallelism": f"replicas x{ws}",
+                           "tile": f"{tinfo.tile_cells} cells x 3 species per block, "
+                                   f"{tinfo.tile_min_blocks} blocks/SM (autotuned)",
                            "l2": "state larger than L2 (no flush needed)" if nf * bpc > 129e6 * 2
                            else "state fits in L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": args.steps, "time_to_residual": ttr}
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def sweep_cases(args):
+    """The uneven-size sweep: each microstructure at each operating point."""
+    from workloads import cases as W
+    structs = W.sweep_structures(args.sweep_2d, args.sweep_3d, scale=args.sweep_scale)
+    pts = W.sweep_operating_points(args.sweep_points)
+    groups = {2: [], 3: []}
+    for st in structs:
+        for I, x in pts:
+            groups[st.dim].append(st.with_(current_A_cm2=I, x_in=x))
+    return groups
+
+
+def main_sweep(args, ws, rank, local):
+    """Many microstructures x operating points: one launch per lattice and
+    step (batched, autotuned tile) against stepping every case in a handle
+    of its own."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1809_01600_gb300 import lbms as L
+    L.load()
+    groups = sweep_cases(args)
+    batches = []
+    for dim in (2, 3):
+        cs = groups[dim]
+        if not cs:
+            continue
+        b = L.Batch.from_cases(cs, precision=args.precision)
+        for k, c in enumerate(cs):
+            b.set_bc(c.x_in, c.current_A_cm2, case=k)
+        batches.append((dim, cs, b))
+    nf = sum(c.n_fluid for _, cs, _ in batches for c in cs)
+    stream = torch.cuda.current_stream()
+    for _, _, b in batches:
+        b.step(args.warmup)
+        b.step(32)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    if dist:
+        dist.barrier()
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _, _, b in batches:
+        b.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    t_dev = ms / 1e3
+    if dist:
+        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    units = nf * 3 * args.steps * ws
+    value = units / t_dev / 1e6
+    tiles = {dim: "%d cells, %d blocks/SM" % (b.info().tile_cells, b.info().tile_min_blocks)
+             for dim, _, b in batches}
+    etas = {dim: b.overpotentials(raise_on_fail=False)[0] for dim, _, b in batches}
+    for _, _, b in batches:
+        b.close()
+
+    # the same cases, one handle each, stepped one after another
+    seq_steps = max(1, min(args.steps, 200))
+    t_seq = 0.0
+    for dim in (2, 3):
+        for c in groups[dim]:
+            s = L.Solver.from_case(c, precision=args.precision)
+            s.set_bc(c.x_in, c.current_A_cm2)
+            s.step(32)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            s.step(seq_steps)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            t_seq += a0.elapsed_time(a1) / 1e3
+            s.close()
+    seq_value = nf * 3 * seq_steps / t_seq / 1e6
+    bpc = {d: bytes_per_cell(d, args.precision) for d in (2, 3)}
+    alg = sum(c.n_fluid * bpc[c.dim] for _, cs, _ in batches for c in cs)
+    achieved = alg / (t_dev / args.steps) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    if rank == 0:
+        n2, n3 = len(groups[2]), len(groups[3])
+        line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(ms / args.steps, 5), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": f"sweep of {args.sweep_2d} 2-D + {args.sweep_3d} 3-D microstructures "
+                                       f"x {args.sweep_points} operating points",
+                           "cases": {"2d": n2, "3d": n3}, "fluid_cells": nf, "precision": args.precision,
+                           "tiles": tiles, "parallelism": f"replicas x{ws}",
+                           "launches_per_step": len(batches)},
+                "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                             "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind},
+                "sequential": {"value": round(seq_value, 2), "unit": METRIC,
+                               "what": "the same cases, one handle each, stepped one after another",
+                               "steps": seq_steps},
+                "speedup_vs_sequential": round(value / seq_value, 2),
+                "eta_V_range": [float(np.nanmin(np.concatenate(list(etas.values())))),
+                                float(np.nanmax(np.concatenate(list(etas.values()))))],
+                "clocks": clk, "gpu_launches": args.steps * len(batches)}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()

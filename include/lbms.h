@@ -118,28 +118,54 @@ typedef struct {
     size_t device_bytes;        /* device memory held by the handle */
     uint64_t h2d_bytes;         /* host-to-device bytes copied so far */
     uint64_t d2h_bytes;         /* device-to-host bytes copied so far */
+    int n_cases;                /* cases in the handle (1 unless made by lbms_create_batch) */
+    int tile_cells;             /* step-kernel tile picked by the autotuner: cells per block */
+    int tile_min_blocks;        /*   and its register budget (resident blocks per SM) */
 } lbms_info;
+/* n_cells and n_fluid sum over all cases; dx_m, dt_s, q_lat, x_in and
+ * current_A_cm2 describe case 0. */
 
 void lbms_default_options(lbms_options *opt);
 
 /* Builds the solver: host properties (Eqs. 40-42, C_t, dx, dt), the fluid
  * cell list and its neighbour table, and the device state.  Nothing runs
  * until lbms_set_bc.  *out receives the handle, or NULL on failure, when
- * lbms_last_error(NULL) gives the reason (per thread). */
+ * lbms_last_error(NULL) gives the reason (per thread).  Same as
+ * lbms_create_batch with one case. */
 lbms_status lbms_create(const lbms_geometry *geom, const lbms_species *species,
                         const lbms_diffusivities *diff, double T_K, double p_Pa,
                         const lbms_options *opt, lbms_ctx **out);
 
+/* Batch of n_cases >= 1 independent anodes (geoms[n_cases], all with the
+ * same dim; sizes, masks and lengths may differ) sharing the gas data and the
+ * options.  Every lbms_step advances all cases with one kernel launch per
+ * step (graph-replayed); the step kernel's tile shape is picked by timing
+ * the compiled candidates on the first full initialisation (lbms_info).  The
+ * paper runs one anode at a time; the batch is the sweep of Section 4.2
+ * (several currents and dilutions) made one launch.  An explicit dt_s needs
+ * the same grid spacing in every case. */
+lbms_status lbms_create_batch(int n_cases, const lbms_geometry *geoms, const lbms_species *species,
+                              const lbms_diffusivities *diff, double T_K, double p_Pa,
+                              const lbms_options *opt, lbms_ctx **out);
+
 /* Boundary data: inlet mole fractions (3, each >= 0, sum 1 within 1e-9;
- * Eq. 36) and current density (A/cm^2, >= 0; Eq. 39).  The first call
- * initialises every fluid cell to f = w X_in (Eq. 29); later calls change
- * the boundary data and keep the state. */
+ * Eq. 36) and current density (A/cm^2, >= 0; Eq. 39), for every case of the
+ * handle.  The first call for a case initialises its fluid cells to
+ * f = w X_in (Eq. 29); later calls change the boundary data and keep the
+ * state. */
 lbms_status lbms_set_bc(lbms_ctx *ctx, const double *x_inlet, double current_A_cm2);
+
+/* As lbms_set_bc for case k only (0 <= k < n_cases).  Stepping needs every
+ * case to have boundary data. */
+lbms_status lbms_batch_set_bc(lbms_ctx *ctx, int k, const double *x_inlet, double current_A_cm2);
 
 /* Restarts from a given field: X is host, 3*N dense (solid entries ignored),
  * f = w X (Eq. 29).  Resets the step counter and the residual snapshot.
- * Needs a prior lbms_set_bc (the boundary data). */
+ * Needs a prior lbms_set_bc (the boundary data).  Acts on case 0. */
 lbms_status lbms_set_fields(lbms_ctx *ctx, const double *X);
+
+/* As lbms_set_fields for case k, X being 3*N_k dense for that case's grid. */
+lbms_status lbms_batch_set_fields(lbms_ctx *ctx, int k, const double *X);
 
 /* Advances nsteps >= 0 time steps (Eq. 28 with the coupling of Eqs. 19-35
  * and the boundaries of Eqs. 36, 39).  Asynchronous: returns once the work is
@@ -149,8 +175,12 @@ lbms_status lbms_step(lbms_ctx *ctx, int64_t nsteps);
 /* Residual r = max_i ||X_i - X_i,snap||_2 / (K ||X_i||_2) over fluid cells
  * (FP64), where the snapshot is the state at the previous residual call (or
  * the last reset); refreshes the snapshot.  K >= 1 is the number of steps
- * since then.  LBMS_EUNSTABLE if NaN/Inf is present (residual set to inf). */
+ * since then.  LBMS_EUNSTABLE if NaN/Inf is present (residual set to inf).
+ * With several cases, the maximum over cases. */
 lbms_status lbms_residual(lbms_ctx *ctx, int K, double *residual);
+
+/* Per-case residuals (residuals[n_cases]); refreshes every snapshot. */
+lbms_status lbms_batch_residuals(lbms_ctx *ctx, int K, double *residuals);
 
 /* Steps until the residual (checked every check_every steps) is <= tol or
  * max_steps are taken.  LBMS_ENOTCONVERGED in the latter case;
@@ -158,21 +188,37 @@ lbms_status lbms_residual(lbms_ctx *ctx, int K, double *residual);
 lbms_status lbms_run_to_residual(lbms_ctx *ctx, double tol, int64_t max_steps,
                                  int64_t *steps_taken, double *final_residual);
 
-/* Fields of the last step on the dense grid, solid voxels zero.
+/* Batch form: steps every case until all residuals are <= tol (or
+ * max_steps).  case_steps[n_cases] receives the step count at which each case
+ * first met tol (-1 if never) and final_residuals[n_cases] the last
+ * residuals; either may be NULL.  LBMS_ENOTCONVERGED if a case missed tol. */
+lbms_status lbms_batch_run_to_residual(lbms_ctx *ctx, double tol, int64_t max_steps,
+                                       int64_t *steps_taken, int64_t *case_steps,
+                                       double *final_residuals);
+
+/* Fields of the last step on the dense grid, solid voxels zero (case 0).
  * X: 3*N mole fractions.  u: 3*dim*N component velocities (m/s,
  * [species][axis][z][y][x], Eq. 20) or NULL.  tau: 3*N relaxation times
  * (Eq. 25) or NULL. */
 lbms_status lbms_get_fields(lbms_ctx *ctx, double *X, double *u, double *tau);
 
+/* As lbms_get_fields for case k (arrays sized for that case's grid). */
+lbms_status lbms_batch_get_fields(lbms_ctx *ctx, int k, double *X, double *u, double *tau);
+
 /* Concentration overpotential (V) by Eq. 43 with X_out the mean over the
  * outlet column (FP64) and X_in the boundary values; x_out_mean (3 doubles)
- * may be NULL.  LBMS_EDEPLETED when a logarithm argument is <= 0. */
+ * may be NULL.  LBMS_EDEPLETED when a logarithm argument is <= 0.  Case 0. */
 lbms_status lbms_overpotential(lbms_ctx *ctx, double *eta_V, double *x_out_mean);
+
+/* Eq. 43 for every case: eta_V[n_cases], x_out_mean[3*n_cases] (or NULL).
+ * A case whose logarithm is undefined gets NaN and the call returns
+ * LBMS_EDEPLETED after filling the others. */
+lbms_status lbms_batch_overpotentials(lbms_ctx *ctx, double *eta_V, double *x_out_mean);
 
 /* Mass balance in FP64: inlet_flux[3] = net mole-fraction units per step
  * that cross the plane between x = 0 and x = 1 toward +x (carried by the
  * last post-collision populations); totals[3] = sum of X over fluid cells.
- * Either pointer may be NULL. */
+ * Either pointer may be NULL.  Case 0. */
 lbms_status lbms_boundary_flux(lbms_ctx *ctx, double *inlet_flux, double *totals);
 
 lbms_status lbms_get_info(const lbms_ctx *ctx, lbms_info *info);

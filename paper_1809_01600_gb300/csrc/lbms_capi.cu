@@ -1,6 +1,7 @@
 // C ABI of the solver (declared in include/lbms.h): validation, host
-// properties, fluid-cell indexing, device state, CUDA-graph stepping,
-// residual loop and the FP64 post-processing of Eq. 43.
+// properties, fluid-cell indexing, batching of cases into one index space,
+// device state, tile autotuning, CUDA-graph stepping, residual loops and
+// the FP64 post-processing of Eq. 43.  A single-case solver is a batch of 1.
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
@@ -13,33 +14,46 @@
 
 #include "../../include/lbms.h"
 #include "lbms_internal.h"
+#include "lbms_kernels.cuh"
 #include "lbms_lattice.cuh"
 #include "lbms_props.cuh"
 
 using namespace lbms;
 
-struct lbms_ctx {
-    // geometry
-    int dim = 2, nx = 0, ny = 0, nz = 0, Q = 9, periodic_x = 0;
+namespace {
+
+struct CaseHost {
+    int nx = 0, ny = 0, nz = 0, periodic_x = 0;
     int64_t N = 0;
     double length_x = 0.0;
     std::vector<int64_t> fluid_cell;  // dense index of each fluid cell, x-fastest order
-    // properties and options
-    GasProps gas{};
+    int base = 0, nf = 0;             // range [base, base + nf) of the kernels' index space
+    int row_first = 0, nrows = 0;     // rows (y, z) in the concatenated row lists
+    double dx = 0.0, dt = 0.0;
+    double x_in[3] = {0, 0, 0};
+    double current = 0.0;
+    double q[3] = {0, 0, 0};          // outlet flux per node per step (lattice units)
+    bool has_bc = false;
+};
+
+}  // namespace
+
+struct lbms_ctx {
+    int dim = 2, Q = 9;
+    std::vector<CaseHost> cases;
+    GasProps gas{};                   // D_eff, C_t, T, p, stoichiometry (dx, dt are per case)
     lbms_options opt{};
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
-    // device state
     Launch L;
     std::vector<std::pair<void*, size_t>> allocs;
     size_t device_bytes = 0;
-    double* host_red = nullptr;  // pinned, 2 * kRedSlots doubles
-    uint64_t h2d = 0, d2h = 0;   // bytes copied across PCIe/C2C so far
-    bool initialized = false;
+    double* host_out = nullptr;       // pinned, cases * kCaseOutSlots doubles
+    std::vector<unsigned char> case_bc;  // packed CaseBC images of all cases
+    bool initialized = false;         // every case has boundary data
+    bool tuned = false;
     int64_t steps = 0;
-    double x_in[3] = {0, 0, 0};
-    double current = 0.0;
-    // CUDA graphs of kGraphSteps steps, one per starting lattice parity
+    uint64_t h2d = 0, d2h = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     std::string err;
 };
@@ -75,6 +89,7 @@ lbms_status cuda_fail(lbms_ctx* c, cudaError_t e, const char* what) {
 
 void* dev_alloc(lbms_ctx* c, size_t bytes) {
     void* p = nullptr;
+    if (bytes == 0) bytes = 16;
     if (c->opt.alloc) {
         p = c->opt.alloc(bytes, c->stream, c->opt.alloc_user);
     } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
@@ -105,13 +120,14 @@ void release(lbms_ctx* c) {
             cudaFree(a.first);
     }
     c->allocs.clear();
-    if (c->host_red) cudaFreeHost(c->host_red);
-    c->host_red = nullptr;
+    if (c->host_out) cudaFreeHost(c->host_out);
+    c->host_out = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
 }
 
-// Eqs. 40-42, C_t and the lattice scaling (dx, dt, D*).
+// Eqs. 40-42 and C_t; the lattice diffusivities follow from the time-step
+// policy (or the explicit dt of the options and the first case's spacing).
 lbms_status compute_props(lbms_ctx* c, const lbms_species* sp, const lbms_diffusivities* df, double T, double p) {
     GasProps& g = c->gas;
     g.T = T;
@@ -150,40 +166,47 @@ lbms_status compute_props(lbms_ctx* c, const lbms_species* sp, const lbms_diffus
             dmin = std::min(dmin, g.D_eff[i][j]);
         }
     g.C_t = p / (kR * T);
-    g.dx = c->periodic_x ? c->length_x / c->nx : c->length_x / (c->nx - 1);
-    g.dt = c->opt.dt_s > 0.0 ? c->opt.dt_s : g.dx * g.dx / (6.0 * dmin);
+    for (auto& cs : c->cases) {
+        cs.dx = cs.periodic_x ? cs.length_x / cs.nx : cs.length_x / (cs.nx - 1);
+        cs.dt = c->opt.dt_s > 0.0 ? c->opt.dt_s : cs.dx * cs.dx / (6.0 * dmin);
+    }
+    const CaseHost& c0 = c->cases[0];
+    for (const auto& cs : c->cases)
+        if (std::fabs(cs.dt / (cs.dx * cs.dx) - c0.dt / (c0.dx * c0.dx)) > 1e-12 * c0.dt / (c0.dx * c0.dx))
+            return fail(c, LBMS_EINVAL, "an explicit dt_s needs the same grid spacing in every case");
+    g.dx = c0.dx;
+    g.dt = c0.dt;
     for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) g.D_lat[i][j] = g.D_eff[i][j] * g.dt / (g.dx * g.dx);
+        for (int j = 0; j < 3; ++j) g.D_lat[i][j] = g.D_eff[i][j] * c0.dt / (c0.dx * c0.dx);
     return LBMS_OK;
 }
 
-// Pull-neighbour table: row i holds, for k = 1..Q-1, the fluid index of the
-// source x - e_k or an NB_* code, padded to nb_width ints.
+// Neighbour rows of one case: row i holds, for k = 1..Q-1, the fluid index of
+// the source x - e_k (in the batch's index space) or an NB_* code.
 template <class Lat>
-void build_neighbours(const lbms_ctx* c, const std::vector<int>& index_of, int64_t S, std::vector<int>& nbr) {
-    const int nf = (int)c->fluid_cell.size();
+void build_neighbours(const CaseHost& cs, const std::vector<int>& index_of, std::vector<int>& nbr) {
     constexpr int NW = nb_width<Lat>();
-    nbr.assign((size_t)NW * S, NB_SOLID);
-    for (int i = 0; i < nf; ++i) {
-        const int64_t cell = c->fluid_cell[i];
-        const int x = (int)(cell % c->nx);
-        const int y = (int)((cell / c->nx) % c->ny);
-        const int z = (int)(cell / ((int64_t)c->nx * c->ny));
+    for (int li = 0; li < cs.nf; ++li) {
+        const int64_t cell = cs.fluid_cell[li];
+        const int x = (int)(cell % cs.nx);
+        const int y = (int)((cell / cs.nx) % cs.ny);
+        const int z = (int)(cell / ((int64_t)cs.nx * cs.ny));
+        int* row = nbr.data() + (size_t)(cs.base + li) * NW;
         for (int k = 1; k < Lat::Q; ++k) {
             int sx = x - Lat::e(k, 0);
-            const int sy = ((y - Lat::e(k, 1)) % c->ny + c->ny) % c->ny;
-            const int sz = ((z - Lat::e(k, 2)) % c->nz + c->nz) % c->nz;
+            const int sy = ((y - Lat::e(k, 1)) % cs.ny + cs.ny) % cs.ny;
+            const int sz = ((z - Lat::e(k, 2)) % cs.nz + cs.nz) % cs.nz;
             int code;
-            if (!c->periodic_x && sx < 0) {
+            if (!cs.periodic_x && sx < 0) {
                 code = NB_INLET;
-            } else if (!c->periodic_x && sx >= c->nx) {
+            } else if (!cs.periodic_x && sx >= cs.nx) {
                 code = NB_OUTLET;
             } else {
-                sx = (sx % c->nx + c->nx) % c->nx;
-                const int j = index_of[((int64_t)sz * c->ny + sy) * c->nx + sx];
-                code = j >= 0 ? j : NB_SOLID;
+                sx = (sx % cs.nx + cs.nx) % cs.nx;
+                const int j = index_of[((int64_t)sz * cs.ny + sy) * cs.nx + sx];
+                code = j >= 0 ? cs.base + j : NB_SOLID;
             }
-            nbr[(size_t)i * NW + (k - 1)] = code;
+            row[k - 1] = code;
         }
     }
 }
@@ -200,11 +223,23 @@ lbms_status validate_bc(lbms_ctx* c, const double* x, double I) {
     return LBMS_OK;
 }
 
-void apply_bc(lbms_ctx* c) {
-    for (int s = 0; s < 3; ++s) c->L.xin[s] = c->x_in[s];
-    outlet_flux_lattice(c->gas, c->current, c->L.q);
-    if (c->periodic_x)
-        for (int s = 0; s < 3; ++s) c->L.q[s] = 0.0;
+// Uploads the device CaseBC entry of case k (inlet values, outlet flux, range).
+lbms_status upload_case_bc(lbms_ctx* c, int k) {
+    const CaseHost& cs = c->cases[k];
+    CaseHostBC h;
+    for (int s = 0; s < 3; ++s) {
+        h.xin[s] = cs.x_in[s];
+        h.q[s] = cs.q[s];
+    }
+    h.base = cs.base;
+    h.nf = cs.nf;
+    const size_t sz = case_bc_size(c->L.precision);
+    pack_case_bc(c->L.precision, h, c->case_bc.data() + k * sz);
+    CK(cudaMemcpyAsync(static_cast<unsigned char*>(c->L.b.cases) + k * sz, c->case_bc.data() + k * sz, sz,
+                       cudaMemcpyHostToDevice, c->stream),
+       "upload boundary data");
+    c->h2d += sz;
+    return LBMS_OK;
 }
 
 // Mole fractions in the device format: double, or a double-float pair whose
@@ -224,21 +259,99 @@ double get_x(int precision, const unsigned char* buf, int64_t S, int64_t idx) {
     return (double)reinterpret_cast<const float*>(buf)[idx] + (double)reinterpret_cast<const float*>(buf)[idx + 3 * S];
 }
 
-// Copies a dense host field (3*N doubles) into X[cur] and restarts from the
-// equilibrium f = w X (h = 0).
-lbms_status upload_field(lbms_ctx* c, const double* X) {
+// Rows (species, and hi/lo words) of the X buffer as a pitched 2-D region.
+int x_rows(int precision) { return precision == LBMS_FP64 ? 3 : 6; }
+size_t x_word(int precision) { return precision == LBMS_FP64 ? sizeof(double) : sizeof(float); }
+
+// Chooses the step kernel's tile shape by timing each variant on the real
+// state: the variants read lattice cur and write lattice cur ^ 1 without
+// swapping, so the state is unchanged; the X copy of cur ^ 1 is restored.
+lbms_status autotune(lbms_ctx* c) {
+    Launch& L = c->L;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0), "autotune event");
+    CK(cudaEventCreate(&e1), "autotune event");
+    float best = std::numeric_limits<float>::infinity();
+    int pick = 0;
+    cudaError_t e = cudaSuccess;
+    for (int v = 0; v < kStepVariants && e == cudaSuccess; ++v) {
+        e = launch_step_variant(L, v, c->stream);  // warm-up
+        if (e != cudaSuccess) break;
+        e = cudaEventRecord(e0, c->stream);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_step_variant(L, v, c->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && ms < best) {
+            best = ms;
+            pick = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune");
+    L.variant = pick;
+    const size_t xbytes = (size_t)3 * L.S * x_size(L.precision);
+    CK(cudaMemcpyAsync(L.b.X[L.cur ^ 1], L.b.X[L.cur], xbytes, cudaMemcpyDeviceToDevice, c->stream), "autotune restore");
+    CK(cudaStreamSynchronize(c->stream), "autotune");
+    c->tuned = true;
+    return LBMS_OK;
+}
+
+// Copies a dense host field of case k (3 * N doubles) into X[cur] and
+// restarts that case from the equilibrium f = w X (h = 0).
+lbms_status upload_field(lbms_ctx* c, int k, const double* X) {
+    CaseHost& cs = c->cases[k];
+    const int prec = c->L.precision;
     const int64_t S = c->L.S;
-    const int nf = c->L.nf;
-    std::vector<unsigned char> buf(3 * (size_t)S * x_size(c->L.precision), 0);
+    const int rows = x_rows(prec);
+    const size_t word = x_word(prec);
+    // a compact [rows][nf] image of the case's slice, copied as a pitched region
+    std::vector<unsigned char> buf((size_t)rows * cs.nf * word, 0);
     for (int s = 0; s < 3; ++s)
-        for (int i = 0; i < nf; ++i) put_x(c->L.precision, buf.data(), S, s * S + i, X[(size_t)s * c->N + c->fluid_cell[i]]);
-    CK(cudaMemcpyAsync(c->L.b.X[c->L.cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream),
+        for (int i = 0; i < cs.nf; ++i) put_x(prec, buf.data(), cs.nf, (int64_t)s * cs.nf + i, X[(size_t)s * cs.N + cs.fluid_cell[i]]);
+    unsigned char* dst = static_cast<unsigned char*>(c->L.b.X[c->L.cur]) + (size_t)cs.base * word;
+    CK(cudaMemcpy2DAsync(dst, S * word, buf.data(), cs.nf * word, cs.nf * word, rows, cudaMemcpyHostToDevice, c->stream),
        "upload mole fractions");
     c->h2d += buf.size();
-    CK(launch_init(c->L, c->stream), "init kernel");
+    CK(launch_init(c->L, cs.base, cs.nf, c->stream), "init kernel");
     CK(cudaStreamSynchronize(c->stream), "init");
-    c->steps = 0;
-    c->initialized = true;
+    return LBMS_OK;
+}
+
+lbms_status set_case_bc(lbms_ctx* c, int k, const double* x_inlet, double current) {
+    lbms_status st = validate_bc(c, x_inlet, current);
+    if (st != LBMS_OK) return st;
+    CaseHost& cs = c->cases[k];
+    for (int s = 0; s < 3; ++s) cs.x_in[s] = x_inlet[s];
+    cs.current = current;
+    if (cs.periodic_x) {
+        for (int s = 0; s < 3; ++s) cs.q[s] = 0.0;
+    } else {
+        GasProps g = c->gas;
+        g.dx = cs.dx;
+        g.dt = cs.dt;
+        outlet_flux_lattice(g, current, cs.q);
+    }
+    st = upload_case_bc(c, k);
+    if (st != LBMS_OK) return st;
+    if (!cs.has_bc) {
+        std::vector<double> X(3 * (size_t)cs.N, 0.0);
+        for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * cs.N, X.begin() + (s + 1) * cs.N, cs.x_in[s]);
+        st = upload_field(c, k, X.data());
+        if (st != LBMS_OK) return st;
+        cs.has_bc = true;
+    }
+    if (!c->initialized) {
+        bool all = true;
+        for (const auto& q : c->cases) all = all && q.has_bc;
+        if (all) {
+            c->initialized = true;
+            c->steps = 0;
+            if (!c->tuned) return autotune(c);
+        }
+    }
     return LBMS_OK;
 }
 
@@ -281,15 +394,63 @@ lbms_status launch_steps(lbms_ctx* c, int64_t n) {
     return LBMS_OK;
 }
 
-lbms_status read_reduction(lbms_ctx* c, int slot, double* out, int nv) {
-    CK(cudaMemcpyAsync(c->host_red, c->L.b.red_out + slot * kRedSlots, nv * sizeof(double),
-                       cudaMemcpyDeviceToHost, c->stream),
+// Reads n doubles of the per-case output buffer starting at offset.
+lbms_status read_case_out(lbms_ctx* c, size_t offset, size_t n) {
+    CK(cudaMemcpyAsync(c->host_out + offset, c->L.b.case_out + offset, n * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->stream),
        "reduction readback");
     CK(cudaStreamSynchronize(c->stream), "reduction");
-    c->d2h += nv * sizeof(double);
-    std::memcpy(out, c->host_red, nv * sizeof(double));
+    c->d2h += n * sizeof(double);
     return LBMS_OK;
 }
+
+// Per-case residuals (refreshing the snapshots); LBMS_EUNSTABLE on NaN/Inf.
+lbms_status case_residuals(lbms_ctx* c, int K, double* r) {
+    const int n = c->L.n_cases;
+    CK(launch_case_residuals(c->L, 1, c->stream), "residual kernels");
+    lbms_status st = read_case_out(c, 0, (size_t)n * 10);
+    if (st != LBMS_OK) return st;
+    bool bad = false;
+    for (int k = 0; k < n; ++k) {
+        const double* o = c->host_out + (size_t)k * 10;
+        if (o[9] > 0.0) {
+            r[k] = std::numeric_limits<double>::infinity();
+            bad = true;
+            continue;
+        }
+        double res = 0.0;
+        for (int s = 0; s < 3; ++s)
+            if (o[3 + s] > 0.0) res = std::max(res, std::sqrt(o[s]) / (K * std::sqrt(o[3 + s])));
+        r[k] = res;
+    }
+    if (bad) return fail(c, LBMS_EUNSTABLE, "non-finite mole fractions after %lld steps", (long long)c->steps);
+    return LBMS_OK;
+}
+
+lbms_status case_boundary(lbms_ctx* c) {
+    CK(launch_case_boundary(c->L, c->stream), "boundary kernel");
+    return read_case_out(c, (size_t)c->L.n_cases * 10, (size_t)c->L.n_cases * 6);
+}
+
+lbms_status overpotential_of(lbms_ctx* c, int k, double* eta, double* xo_out) {
+    const CaseHost& cs = c->cases[k];
+    const double* o = c->host_out + (size_t)c->L.n_cases * 10 + (size_t)k * 6;
+    double xo[3];
+    for (int s = 0; s < 3; ++s) xo[s] = o[3 + s] / cs.nrows;
+    if (xo_out)
+        for (int s = 0; s < 3; ++s) xo_out[s] = xo[s];
+    const double a = cs.x_in[0] * xo[1];
+    const double b = xo[0] * cs.x_in[1];
+    if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b)) {
+        if (eta) *eta = std::numeric_limits<double>::quiet_NaN();
+        return fail(c, LBMS_EDEPLETED, "case %d: Eq. 43 undefined: X_in = (%g, %g), X_out = (%g, %g)", k, cs.x_in[0],
+                    cs.x_in[1], xo[0], xo[1]);
+    }
+    if (eta) *eta = kR * c->gas.T / (c->gas.electrons * kF) * std::log(a / b);
+    return LBMS_OK;
+}
+
+bool bad_case(const lbms_ctx* c, int k) { return !c || k < 0 || k >= (int)c->cases.size(); }
 
 }  // namespace
 
@@ -322,14 +483,14 @@ const char* lbms_status_string(lbms_status s) {
 
 const char* lbms_last_error(const lbms_ctx* c) { return c ? c->err.c_str() : t_create_error.c_str(); }
 
-lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const lbms_diffusivities* df, double T_K,
-                        double p_Pa, const lbms_options* opt, lbms_ctx** out) {
+lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbms_species* sp,
+                              const lbms_diffusivities* df, double T_K, double p_Pa, const lbms_options* opt,
+                              lbms_ctx** out) {
     if (!out) return LBMS_EINVAL;
     *out = nullptr;
     t_create_error.clear();
     lbms_ctx* c = new (std::nothrow) lbms_ctx();
     if (!c) return LBMS_ENOMEM;
-    lbms_status st = LBMS_OK;
     auto bail = [&](lbms_status s) {
         // the message stays readable through lbms_last_error(NULL) on this thread
         t_create_error = c->err;
@@ -342,15 +503,22 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     else
         lbms_default_options(&c->opt);
     if (c->opt.check_every <= 0) c->opt.check_every = 100;
-    if (!geom) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
+    if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
+    if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
-    if (geom->dim != 2 && geom->dim != 3) return bail(fail(c, LBMS_EINVAL, "dim must be 2 or 3"));
-    if (geom->nx < 1 || geom->ny < 1 || geom->nz < 1) return bail(fail(c, LBMS_EINVAL, "nx, ny, nz must be >= 1"));
-    if (geom->dim == 2 && geom->nz != 1) return bail(fail(c, LBMS_EINVAL, "nz must be 1 when dim = 2"));
-    if (!geom->periodic_x && geom->nx < 3) return bail(fail(c, LBMS_EINVAL, "nx must be >= 3 with an inlet and outlet"));
-    if (!geom->solid) return bail(fail(c, LBMS_EINVAL, "solid mask is NULL"));
-    if (!(geom->length_x_m > 0.0) || !std::isfinite(geom->length_x_m))
-        return bail(fail(c, LBMS_EINVAL, "length_x_m must be finite and > 0"));
+    const int dim = geoms[0].dim;
+    if (dim != 2 && dim != 3) return bail(fail(c, LBMS_EINVAL, "dim must be 2 or 3"));
+    for (int k = 0; k < n_cases; ++k) {
+        const lbms_geometry* g = &geoms[k];
+        if (g->dim != dim) return bail(fail(c, LBMS_EINVAL, "case %d: every case of a batch needs the same dim", k));
+        if (g->nx < 1 || g->ny < 1 || g->nz < 1) return bail(fail(c, LBMS_EINVAL, "case %d: nx, ny, nz must be >= 1", k));
+        if (dim == 2 && g->nz != 1) return bail(fail(c, LBMS_EINVAL, "case %d: nz must be 1 when dim = 2", k));
+        if (!g->periodic_x && g->nx < 3)
+            return bail(fail(c, LBMS_EINVAL, "case %d: nx must be >= 3 with an inlet and outlet", k));
+        if (!g->solid) return bail(fail(c, LBMS_EINVAL, "case %d: solid mask is NULL", k));
+        if (!(g->length_x_m > 0.0) || !std::isfinite(g->length_x_m))
+            return bail(fail(c, LBMS_EINVAL, "case %d: length_x_m must be finite and > 0", k));
+    }
     if (sp->n != 3) return bail(fail(c, LBMS_EINVAL, "only ternary mixtures (n = 3) are supported"));
     if (!sp->stoich || sp->electrons <= 0) return bail(fail(c, LBMS_EINVAL, "stoich and electrons > 0 are required"));
     if ((!df || !df->D_binary_m2s || (df->pore_diameter_m > 0.0)) && !sp->molar_mass)
@@ -369,47 +537,58 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     if (c->opt.coupling != LBMS_COUPLING_MS && c->opt.coupling != LBMS_COUPLING_TAU_ONLY)
         return bail(fail(c, LBMS_EINVAL, "unknown coupling"));
 
-    c->dim = geom->dim;
-    c->nx = geom->nx;
-    c->ny = geom->ny;
-    c->nz = geom->nz;
-    c->Q = geom->dim == 2 ? D2Q9::Q : D3Q19::Q;
-    c->periodic_x = geom->periodic_x ? 1 : 0;
-    c->length_x = geom->length_x_m;
-    c->N = (int64_t)c->nx * c->ny * c->nz;
+    c->dim = dim;
+    c->Q = dim == 2 ? D2Q9::Q : D3Q19::Q;
     c->stream = static_cast<cudaStream_t>(c->opt.stream);
 
-    // fluid cells, boundary columns
-    std::vector<int> index_of((size_t)c->N, -1);
-    for (int64_t cell = 0; cell < c->N; ++cell) {
-        if (geom->solid[cell]) continue;
-        if (c->fluid_cell.size() >= (size_t)std::numeric_limits<int>::max() / 2)
+    // fluid cells and boundary rows of every case, laid out one after another
+    c->cases.resize(n_cases);
+    std::vector<std::vector<int>> index_of(n_cases);
+    std::vector<int> rows_x0, rows_x1, rows_out;
+    int64_t next = 0;
+    for (int k = 0; k < n_cases; ++k) {
+        const lbms_geometry* g = &geoms[k];
+        CaseHost& cs = c->cases[k];
+        cs.nx = g->nx;
+        cs.ny = g->ny;
+        cs.nz = g->nz;
+        cs.periodic_x = g->periodic_x ? 1 : 0;
+        cs.length_x = g->length_x_m;
+        cs.N = (int64_t)cs.nx * cs.ny * cs.nz;
+        index_of[k].assign((size_t)cs.N, -1);
+        for (int64_t cell = 0; cell < cs.N; ++cell) {
+            if (g->solid[cell]) continue;
+            index_of[k][cell] = (int)cs.fluid_cell.size();
+            cs.fluid_cell.push_back(cell);
+        }
+        if (cs.fluid_cell.empty()) return bail(fail(c, LBMS_EINVAL, "case %d: the mask has no fluid cell", k));
+        cs.nf = (int)cs.fluid_cell.size();
+        cs.base = (int)next;
+        next += ((int64_t)cs.nf + kCaseAlign - 1) / kCaseAlign * kCaseAlign;
+        if (next >= (int64_t)std::numeric_limits<int>::max() / 32)
             return bail(fail(c, LBMS_EINVAL, "too many fluid cells for 32-bit indices"));
-        index_of[cell] = (int)c->fluid_cell.size();
-        c->fluid_cell.push_back(cell);
+        cs.row_first = (int)rows_x0.size();
+        cs.nrows = cs.ny * cs.nz;
+        for (int r = 0; r < cs.nrows; ++r) {
+            const int64_t b = (int64_t)r * cs.nx;
+            const int i0 = index_of[k][b], i1 = cs.nx > 1 ? index_of[k][b + 1] : -1, io = index_of[k][b + cs.nx - 1];
+            if (!cs.periodic_x && (i0 < 0 || io < 0))
+                return bail(fail(c, LBMS_EINVAL, "case %d: inlet (x = 0) and outlet (x = nx-1) columns must be fluid", k));
+            rows_x0.push_back(i0 >= 0 ? cs.base + i0 : -1);
+            rows_x1.push_back(i1 >= 0 ? cs.base + i1 : -1);
+            rows_out.push_back(io >= 0 ? cs.base + io : -1);
+        }
     }
-    if (c->fluid_cell.empty()) return bail(fail(c, LBMS_EINVAL, "the mask has no fluid cell"));
-    const int nrows = c->ny * c->nz;
-    std::vector<int> rows(3 * (size_t)nrows, -1);
-    for (int r = 0; r < nrows; ++r) {
-        const int64_t base = (int64_t)r * c->nx;
-        rows[r] = index_of[base];
-        rows[nrows + r] = c->nx > 1 ? index_of[base + 1] : -1;
-        rows[2 * nrows + r] = index_of[base + c->nx - 1];
-        if (!c->periodic_x && (rows[r] < 0 || rows[2 * nrows + r] < 0))
-            return bail(fail(c, LBMS_EINVAL, "inlet (x = 0) and outlet (x = nx-1) columns must be fluid"));
-    }
-
-    st = compute_props(c, sp, df, T_K, p_Pa);
+    lbms_status st = compute_props(c, sp, df, T_K, p_Pa);
     if (st != LBMS_OK) return bail(st);
 
-    // device state
     Launch& L = c->L;
-    L.dim = c->dim;
+    L.dim = dim;
     L.precision = c->opt.precision;
-    L.nf = (int)c->fluid_cell.size();
-    L.S = ((int64_t)L.nf + 31) / 32 * 32;
-    L.nrows = nrows;
+    L.n_cases = n_cases;
+    L.ncells = (int)next;
+    L.S = ((int64_t)L.ncells + 31) / 32 * 32;
+    L.total_rows = (int)rows_x0.size();
     if ((int64_t)c->Q * L.S >= (int64_t)std::numeric_limits<int>::max())
         return bail(fail(c, LBMS_EINVAL, "too many fluid cells: Q x cells must stay below 2^31"));
     L.D12 = c->gas.D_lat[0][1];
@@ -419,6 +598,29 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     L.tau_min = c->opt.tau_min;
     L.tau_max = c->opt.tau_max;
     L.drift = c->opt.coupling == LBMS_COUPLING_MS ? 1 : 0;
+
+    // reduction segments and block -> case tables
+    std::vector<int2> segs, case_segs(n_cases), case_rows(n_cases);
+    for (int k = 0; k < n_cases; ++k) {
+        const CaseHost& cs = c->cases[k];
+        case_segs[k] = make_int2((int)segs.size(), 0);
+        for (int j = 0; j < cs.nf; j += kSegCells) segs.push_back(make_int2(cs.base + j, std::min(kSegCells, cs.nf - j)));
+        case_segs[k].y = (int)segs.size() - case_segs[k].x;
+        case_rows[k] = make_int2(cs.row_first, cs.nrows);
+    }
+    L.n_segs = (int)segs.size();
+    std::vector<std::vector<int>> blk_case(kStepVariants);
+    for (int v = 0; v < kStepVariants; ++v) {
+        const int W = kVariantCells[v];
+        L.nblk[v] = L.ncells / W;
+        blk_case[v].resize(L.nblk[v]);
+        int k = 0;
+        for (int b = 0; b < L.nblk[v]; ++b) {
+            while (k + 1 < n_cases && b * W >= c->cases[k + 1].base) ++k;
+            blk_case[v][b] = k;
+        }
+    }
+
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
@@ -426,203 +628,277 @@ lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const
     if (cudaDeviceGetAttribute(&smc, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && smc > 0) L.sm_count = smc;
     e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "create capture stream"));
-    e = cudaMallocHost(&c->host_red, 2 * kRedSlots * sizeof(double));
+    e = cudaMallocHost(&c->host_out, (size_t)n_cases * kCaseOutSlots * sizeof(double));
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "pinned readback buffer"));
 
+    const int nbw = dim == 2 ? nb_width<D2Q9>() : nb_width<D3Q19>();
     const size_t fbytes = (size_t)3 * c->Q * L.S * pop_size(L.precision);
     const size_t xbytes = (size_t)3 * L.S * x_size(L.precision);
+    const size_t sbytes = (size_t)3 * L.S * sizeof(double);
+    const size_t cbytes = (size_t)n_cases * case_bc_size(L.precision);
     for (int k = 0; k < 2; ++k) {
         L.b.f[k] = dev_alloc(c, fbytes);
         L.b.X[k] = dev_alloc(c, xbytes);
     }
-    const size_t sbytes = (size_t)3 * L.S * sizeof(double);
     L.b.snap = static_cast<double*>(dev_alloc(c, sbytes));
-    const int nbw = c->dim == 2 ? nb_width<D2Q9>() : nb_width<D3Q19>();
     L.b.nbr = static_cast<int*>(dev_alloc(c, (size_t)nbw * L.S * sizeof(int)));
-    L.b.rows = static_cast<int*>(dev_alloc(c, 3 * (size_t)nrows * sizeof(int)));
-    L.b.red_partials = static_cast<double*>(dev_alloc(c, (size_t)kRedMaxBlocks * kRedSlots * sizeof(double)));
-    L.b.red_counter = static_cast<unsigned int*>(dev_alloc(c, 4 * sizeof(unsigned int)));
-    L.b.red_out = static_cast<double*>(dev_alloc(c, 2 * kRedSlots * sizeof(double)));
-    if (!L.b.f[0] || !L.b.f[1] || !L.b.X[0] || !L.b.X[1] || !L.b.snap || !L.b.nbr || !L.b.rows ||
-        !L.b.red_partials || !L.b.red_counter || !L.b.red_out)
-        return bail(fail(c, LBMS_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes + 3 * xbytes));
+    L.b.rows = static_cast<int*>(dev_alloc(c, 3 * (size_t)L.total_rows * sizeof(int)));
+    L.b.case_rows = static_cast<int2*>(dev_alloc(c, (size_t)n_cases * sizeof(int2)));
+    L.b.cases = dev_alloc(c, cbytes);
+    for (int v = 0; v < kStepVariants; ++v) L.b.blk_case[v] = static_cast<int*>(dev_alloc(c, (size_t)L.nblk[v] * sizeof(int)));
+    L.b.segs = static_cast<int2*>(dev_alloc(c, segs.size() * sizeof(int2)));
+    L.b.case_segs = static_cast<int2*>(dev_alloc(c, (size_t)n_cases * sizeof(int2)));
+    L.b.partials = static_cast<double*>(dev_alloc(c, segs.size() * 10 * sizeof(double)));
+    L.b.case_out = static_cast<double*>(dev_alloc(c, (size_t)n_cases * kCaseOutSlots * sizeof(double)));
+    bool ok = L.b.f[0] && L.b.f[1] && L.b.X[0] && L.b.X[1] && L.b.snap && L.b.nbr && L.b.rows && L.b.case_rows &&
+              L.b.cases && L.b.segs && L.b.case_segs && L.b.partials && L.b.case_out;
+    for (int v = 0; v < kStepVariants; ++v) ok = ok && L.b.blk_case[v];
+    if (!ok) return bail(fail(c, LBMS_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes + 2 * xbytes + sbytes));
 
-    std::vector<int> nbr;
-    if (c->dim == 2)
-        build_neighbours<D2Q9>(c, index_of, L.S, nbr);
-    else
-        build_neighbours<D3Q19>(c, index_of, L.S, nbr);
-    e = cudaMemcpyAsync(L.b.nbr, nbr.data(), nbr.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(L.b.rows, rows.data(), rows.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.b.red_counter, 0, 4 * sizeof(unsigned int), c->stream);
+    std::vector<int> nbr((size_t)nbw * L.S, NB_SOLID);
+    for (int k = 0; k < n_cases; ++k) {
+        if (dim == 2)
+            build_neighbours<D2Q9>(c->cases[k], index_of[k], nbr);
+        else
+            build_neighbours<D3Q19>(c->cases[k], index_of[k], nbr);
+    }
+    std::vector<int> rows;
+    rows.reserve(3 * rows_x0.size());
+    rows.insert(rows.end(), rows_x0.begin(), rows_x0.end());
+    rows.insert(rows.end(), rows_x1.begin(), rows_x1.end());
+    rows.insert(rows.end(), rows_out.begin(), rows_out.end());
+    c->case_bc.assign(cbytes, 0);
+    auto up = [&](void* dst, const void* src, size_t n) {
+        if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream);
+        c->h2d += n;
+    };
+    up(L.b.nbr, nbr.data(), nbr.size() * sizeof(int));
+    up(L.b.rows, rows.data(), rows.size() * sizeof(int));
+    up(L.b.case_rows, case_rows.data(), case_rows.size() * sizeof(int2));
+    up(L.b.segs, segs.data(), segs.size() * sizeof(int2));
+    up(L.b.case_segs, case_segs.data(), case_segs.size() * sizeof(int2));
+    for (int v = 0; v < kStepVariants; ++v) up(L.b.blk_case[v], blk_case[v].data(), blk_case[v].size() * sizeof(int));
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.f[k], 0, fbytes, c->stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.X[k], 0, xbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(L.b.snap, 0, sbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.b.cases, 0, cbytes, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload of the neighbour table"));
-    c->h2d += nbr.size() * sizeof(int) + rows.size() * sizeof(int);
+    for (int k = 0; k < n_cases && st == LBMS_OK; ++k) st = upload_case_bc(c, k);
+    if (st != LBMS_OK) return bail(st);
     *out = c;
     return LBMS_OK;
 }
 
+lbms_status lbms_create(const lbms_geometry* geom, const lbms_species* sp, const lbms_diffusivities* df, double T_K,
+                        double p_Pa, const lbms_options* opt, lbms_ctx** out) {
+    if (!geom) {
+        if (out) *out = nullptr;
+        t_create_error = "geometry is NULL";
+        return LBMS_EINVAL;
+    }
+    return lbms_create_batch(1, geom, sp, df, T_K, p_Pa, opt, out);
+}
+
 lbms_status lbms_set_bc(lbms_ctx* c, const double* x_inlet, double current_A_cm2) {
     if (!c || c->allocs.empty()) return fail(c, LBMS_ESTATE, "handle has no device state");
-    lbms_status st = validate_bc(c, x_inlet, current_A_cm2);
-    if (st != LBMS_OK) return st;
-    for (int s = 0; s < 3; ++s) c->x_in[s] = x_inlet[s];
-    c->current = current_A_cm2;
-    apply_bc(c);
-    drop_graphs(c);
-    if (!c->initialized) {
-        std::vector<double> X(3 * (size_t)c->N, 0.0);
-        for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * c->N, X.begin() + (s + 1) * c->N, c->x_in[s]);
-        return upload_field(c, X.data());
+    for (int k = 0; k < (int)c->cases.size(); ++k) {
+        lbms_status st = set_case_bc(c, k, x_inlet, current_A_cm2);
+        if (st != LBMS_OK) return st;
     }
     return LBMS_OK;
 }
 
-lbms_status lbms_set_fields(lbms_ctx* c, const double* X) {
+lbms_status lbms_batch_set_bc(lbms_ctx* c, int k, const double* x_inlet, double current_A_cm2) {
     if (!c || c->allocs.empty()) return fail(c, LBMS_ESTATE, "handle has no device state");
-    if (!c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc before lbms_set_fields");
+    if (bad_case(c, k)) return fail(c, LBMS_EINVAL, "case index %d out of range", k);
+    return set_case_bc(c, k, x_inlet, current_A_cm2);
+}
+
+lbms_status lbms_batch_set_fields(lbms_ctx* c, int k, const double* X) {
+    if (!c || c->allocs.empty()) return fail(c, LBMS_ESTATE, "handle has no device state");
+    if (bad_case(c, k)) return fail(c, LBMS_EINVAL, "case index %d out of range", k);
+    if (!c->cases[k].has_bc) return fail(c, LBMS_ESTATE, "set the boundary data of case %d first", k);
     if (!X) return fail(c, LBMS_EINVAL, "X is NULL");
-    return upload_field(c, X);
+    lbms_status st = upload_field(c, k, X);
+    if (st == LBMS_OK) c->steps = 0;
+    return st;
+}
+
+lbms_status lbms_set_fields(lbms_ctx* c, const double* X) {
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc before lbms_set_fields");
+    return lbms_batch_set_fields(c, 0, X);
 }
 
 lbms_status lbms_step(lbms_ctx* c, int64_t nsteps) {
-    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "set the boundary data of every case first");
     if (nsteps < 0) return fail(c, LBMS_EINVAL, "nsteps must be >= 0");
     return launch_steps(c, nsteps);
+}
+
+lbms_status lbms_batch_residuals(lbms_ctx* c, int K, double* residuals) {
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "set the boundary data of every case first");
+    if (K < 1 || !residuals) return fail(c, LBMS_EINVAL, "need K >= 1 and a residual array");
+    return case_residuals(c, K, residuals);
 }
 
 lbms_status lbms_residual(lbms_ctx* c, int K, double* residual) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
     if (K < 1 || !residual) return fail(c, LBMS_EINVAL, "need K >= 1 and a residual pointer");
-    CK(launch_residual(c->L, 1, c->stream), "residual kernel");
-    double r[10];
-    lbms_status st = read_reduction(c, kRedResidual, r, 10);
-    if (st != LBMS_OK) return st;
-    if (r[9] > 0.0) {
-        *residual = std::numeric_limits<double>::infinity();
-        return fail(c, LBMS_EUNSTABLE, "%.0f non-finite mole fractions after %lld steps", r[9], (long long)c->steps);
+    std::vector<double> r(c->cases.size());
+    lbms_status st = case_residuals(c, K, r.data());
+    double m = 0.0;
+    for (double v : r) m = std::max(m, v);
+    *residual = st == LBMS_EUNSTABLE ? std::numeric_limits<double>::infinity() : m;
+    return st;
+}
+
+lbms_status lbms_batch_run_to_residual(lbms_ctx* c, double tol, int64_t max_steps, int64_t* steps_taken,
+                                       int64_t* case_steps, double* final_residuals) {
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "set the boundary data of every case first");
+    if (!(tol >= 0.0) || max_steps < 0) return fail(c, LBMS_EINVAL, "need tol >= 0 and max_steps >= 0");
+    const int n = (int)c->cases.size();
+    const int K = c->opt.check_every;
+    std::vector<double> r(n, std::numeric_limits<double>::infinity());
+    std::vector<int64_t> met(n, -1);
+    int64_t done = 0;
+    CK(launch_case_residuals(c->L, 1, c->stream), "residual kernels");  // snapshots start here
+    lbms_status st = LBMS_OK;
+    bool all = false;
+    while (done < max_steps && !all) {
+        const int64_t k = std::min<int64_t>(K, max_steps - done);
+        st = launch_steps(c, k);
+        if (st != LBMS_OK) break;
+        done += k;
+        st = case_residuals(c, (int)k, r.data());
+        if (st != LBMS_OK) break;
+        all = true;
+        for (int q = 0; q < n; ++q) {
+            if (met[q] < 0 && r[q] <= tol) met[q] = done;
+            all = all && met[q] >= 0;
+        }
     }
-    double res = 0.0;
-    for (int s = 0; s < 3; ++s)
-        if (r[3 + s] > 0.0) res = std::max(res, std::sqrt(r[s]) / (K * std::sqrt(r[3 + s])));
-    *residual = res;
+    if (steps_taken) *steps_taken = done;
+    if (case_steps)
+        for (int q = 0; q < n; ++q) case_steps[q] = met[q];
+    if (final_residuals)
+        for (int q = 0; q < n; ++q) final_residuals[q] = r[q];
+    if (st != LBMS_OK) return st;
+    if (!all) return fail(c, LBMS_ENOTCONVERGED, "not every case reached %.3e after %lld steps", tol, (long long)done);
     return LBMS_OK;
 }
 
 lbms_status lbms_run_to_residual(lbms_ctx* c, double tol, int64_t max_steps, int64_t* steps_taken,
                                  double* final_residual) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
-    if (!(tol >= 0.0) || max_steps < 0) return fail(c, LBMS_EINVAL, "need tol >= 0 and max_steps >= 0");
-    const int K = c->opt.check_every;
-    double r = std::numeric_limits<double>::infinity();
-    int64_t done = 0;
-    // the snapshot starts at the current state
-    CK(launch_residual(c->L, 1, c->stream), "residual kernel");
-    lbms_status st = LBMS_OK;
-    while (done < max_steps) {
-        const int64_t k = std::min<int64_t>(K, max_steps - done);
-        st = launch_steps(c, k);
-        if (st != LBMS_OK) break;
-        done += k;
-        st = lbms_residual(c, (int)k, &r);
-        if (st != LBMS_OK) break;
-        if (r <= tol) break;
+    std::vector<double> r(c->cases.size());
+    lbms_status st = lbms_batch_run_to_residual(c, tol, max_steps, steps_taken, nullptr, r.data());
+    if (final_residual) {
+        double m = 0.0;
+        for (double v : r) m = std::max(m, v);
+        *final_residual = m;
     }
-    if (steps_taken) *steps_taken = done;
-    if (final_residual) *final_residual = r;
-    if (st != LBMS_OK) return st;
-    if (!(r <= tol)) return fail(c, LBMS_ENOTCONVERGED, "residual %.3e above %.3e after %lld steps", r, tol, (long long)done);
+    return st;
+}
+
+lbms_status lbms_batch_get_fields(lbms_ctx* c, int k, double* X, double* u, double* tau) {
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "set the boundary data of every case first");
+    if (bad_case(c, k)) return fail(c, LBMS_EINVAL, "case index %d out of range", k);
+    const CaseHost& cs = c->cases[k];
+    const int64_t S = c->L.S;
+    const int prec = c->L.precision;
+    if (X) {
+        const int rows = x_rows(prec);
+        const size_t word = x_word(prec);
+        std::vector<unsigned char> b((size_t)rows * cs.nf * word);
+        const unsigned char* src = static_cast<const unsigned char*>(c->L.b.X[c->L.cur]) + (size_t)cs.base * word;
+        CK(cudaMemcpy2DAsync(b.data(), cs.nf * word, src, S * word, cs.nf * word, rows, cudaMemcpyDeviceToHost, c->stream),
+           "read X");
+        CK(cudaStreamSynchronize(c->stream), "read X");
+        c->d2h += b.size();
+        std::fill(X, X + 3 * cs.N, 0.0);
+        for (int s = 0; s < 3; ++s)
+            for (int i = 0; i < cs.nf; ++i) X[s * cs.N + cs.fluid_cell[i]] = get_x(prec, b.data(), cs.nf, (int64_t)s * cs.nf + i);
+    }
+    if (u || tau) {
+        const size_t es = field_size(prec);
+        const int rows = 3 + 3 * c->dim;
+        if (!c->L.b.fields) {
+            c->L.b.fields = dev_alloc(c, (size_t)rows * S * es);
+            if (!c->L.b.fields) return fail(c, LBMS_ENOMEM, "fields buffer");
+        }
+        CK(launch_fields(c->L, c->stream), "fields kernel");
+        std::vector<unsigned char> b((size_t)rows * cs.nf * es);
+        const unsigned char* src = static_cast<const unsigned char*>(c->L.b.fields) + (size_t)cs.base * es;
+        CK(cudaMemcpy2DAsync(b.data(), cs.nf * es, src, S * es, cs.nf * es, rows, cudaMemcpyDeviceToHost, c->stream),
+           "read fields");
+        CK(cudaStreamSynchronize(c->stream), "read fields");
+        c->d2h += b.size();
+        auto val = [&](int row, int i) {
+            const size_t idx = (size_t)row * cs.nf + i;
+            return prec == LBMS_FP64 ? reinterpret_cast<const double*>(b.data())[idx]
+                                     : (double)reinterpret_cast<const float*>(b.data())[idx];
+        };
+        if (tau) {
+            std::fill(tau, tau + 3 * cs.N, 0.0);
+            for (int s = 0; s < 3; ++s)
+                for (int i = 0; i < cs.nf; ++i) tau[s * cs.N + cs.fluid_cell[i]] = val(s, i);
+        }
+        if (u) {
+            const double scale = cs.dx / cs.dt;
+            std::fill(u, u + 3 * (size_t)c->dim * cs.N, 0.0);
+            for (int s = 0; s < 3; ++s)
+                for (int d = 0; d < c->dim; ++d)
+                    for (int i = 0; i < cs.nf; ++i)
+                        u[(s * c->dim + d) * cs.N + cs.fluid_cell[i]] = scale * val(3 + s * c->dim + d, i);
+        }
+    }
     return LBMS_OK;
 }
 
 lbms_status lbms_get_fields(lbms_ctx* c, double* X, double* u, double* tau) {
-    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
-    const int64_t S = c->L.S;
-    const int nf = c->L.nf;
-    const int prec = c->L.precision;
-    if (X) {
-        std::vector<unsigned char> b(3 * (size_t)S * x_size(prec));
-        CK(cudaMemcpyAsync(b.data(), c->L.b.X[c->L.cur], b.size(), cudaMemcpyDeviceToHost, c->stream), "read X");
-        CK(cudaStreamSynchronize(c->stream), "read X");
-        c->d2h += b.size();
-        std::fill(X, X + 3 * c->N, 0.0);
-        for (int s = 0; s < 3; ++s)
-            for (int i = 0; i < nf; ++i) X[s * c->N + c->fluid_cell[i]] = get_x(prec, b.data(), S, s * S + i);
+    return lbms_batch_get_fields(c, 0, X, u, tau);
+}
+
+lbms_status lbms_batch_overpotentials(lbms_ctx* c, double* eta_V, double* x_out_mean) {
+    if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "set the boundary data of every case first");
+    if (!eta_V) return fail(c, LBMS_EINVAL, "eta_V is NULL");
+    lbms_status st = case_boundary(c);
+    if (st != LBMS_OK) return st;
+    lbms_status worst = LBMS_OK;
+    for (int k = 0; k < (int)c->cases.size(); ++k) {
+        if (c->cases[k].periodic_x) {
+            eta_V[k] = std::numeric_limits<double>::quiet_NaN();
+            worst = fail(c, LBMS_EINVAL, "case %d is periodic in x and has no outlet", k);
+            continue;
+        }
+        st = overpotential_of(c, k, eta_V + k, x_out_mean ? x_out_mean + 3 * k : nullptr);
+        if (st != LBMS_OK) worst = st;
     }
-    const size_t es = field_size(prec);
-    auto to_double = [&](const std::vector<unsigned char>& b, int64_t idx) {
-        return prec == LBMS_FP64 ? reinterpret_cast<const double*>(b.data())[idx]
-                                 : (double)reinterpret_cast<const float*>(b.data())[idx];
-    };
-    if (u || tau) {
-        if (!c->L.b.fields) {
-            c->L.b.fields = dev_alloc(c, (size_t)(3 + 3 * c->dim) * S * es);
-            if (!c->L.b.fields) return fail(c, LBMS_ENOMEM, "fields buffer");
-        }
-        CK(launch_fields(c->L, c->stream), "fields kernel");
-        std::vector<unsigned char> b((size_t)(3 + 3 * c->dim) * S * es);
-        CK(cudaMemcpyAsync(b.data(), c->L.b.fields, b.size(), cudaMemcpyDeviceToHost, c->stream), "read fields");
-        CK(cudaStreamSynchronize(c->stream), "read fields");
-        c->d2h += b.size();
-        if (tau) {
-            std::fill(tau, tau + 3 * c->N, 0.0);
-            for (int s = 0; s < 3; ++s)
-                for (int i = 0; i < nf; ++i) tau[s * c->N + c->fluid_cell[i]] = to_double(b, s * S + i);
-        }
-        if (u) {
-            const double scale = c->gas.dx / c->gas.dt;
-            std::fill(u, u + 3 * (size_t)c->dim * c->N, 0.0);
-            for (int s = 0; s < 3; ++s)
-                for (int d = 0; d < c->dim; ++d)
-                    for (int i = 0; i < nf; ++i)
-                        u[(s * c->dim + d) * c->N + c->fluid_cell[i]] =
-                            scale * to_double(b, (3 + s * c->dim + d) * S + i);
-        }
-    }
-    return LBMS_OK;
+    return worst;
 }
 
 lbms_status lbms_overpotential(lbms_ctx* c, double* eta_V, double* x_out_mean) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
-    if (c->periodic_x) return fail(c, LBMS_EINVAL, "a box periodic in x has no outlet");
-    CK(launch_boundary(c->L, c->stream), "boundary kernel");
-    double r[6];
-    lbms_status st = read_reduction(c, kRedBoundary, r, 6);
+    if (c->cases[0].periodic_x) return fail(c, LBMS_EINVAL, "a box periodic in x has no outlet");
+    lbms_status st = case_boundary(c);
     if (st != LBMS_OK) return st;
-    double xo[3];
-    for (int s = 0; s < 3; ++s) xo[s] = r[3 + s] / c->L.nrows;
-    if (x_out_mean)
-        for (int s = 0; s < 3; ++s) x_out_mean[s] = xo[s];
-    const double a = c->x_in[0] * xo[1];
-    const double b = xo[0] * c->x_in[1];
-    if (!(a > 0.0) || !(b > 0.0) || !std::isfinite(a) || !std::isfinite(b)) {
-        if (eta_V) *eta_V = std::numeric_limits<double>::quiet_NaN();
-        return fail(c, LBMS_EDEPLETED, "Eq. 43 undefined: X_in = (%g, %g), X_out = (%g, %g)", c->x_in[0], c->x_in[1],
-                    xo[0], xo[1]);
-    }
-    if (eta_V) *eta_V = kR * c->gas.T / (c->gas.electrons * kF) * std::log(a / b);
-    return LBMS_OK;
+    return overpotential_of(c, 0, eta_V, x_out_mean);
 }
 
 lbms_status lbms_boundary_flux(lbms_ctx* c, double* inlet_flux, double* totals) {
     if (!c || !c->initialized) return fail(c, LBMS_ESTATE, "call lbms_set_bc first");
     if (inlet_flux) {
-        CK(launch_boundary(c->L, c->stream), "boundary kernel");
-        double r[6];
-        lbms_status st = read_reduction(c, kRedBoundary, r, 6);
+        lbms_status st = case_boundary(c);
         if (st != LBMS_OK) return st;
-        for (int s = 0; s < 3; ++s) inlet_flux[s] = r[s];
+        const double* o = c->host_out + (size_t)c->L.n_cases * 10;
+        for (int s = 0; s < 3; ++s) inlet_flux[s] = o[s];
     }
     if (totals) {
-        CK(launch_residual(c->L, 0, c->stream), "sum kernel");
-        double r[10];
-        lbms_status st = read_reduction(c, kRedResidual, r, 10);
+        CK(launch_case_residuals(c->L, 0, c->stream), "sum kernels");
+        lbms_status st = read_case_out(c, 0, (size_t)c->L.n_cases * 10);
         if (st != LBMS_OK) return st;
-        for (int s = 0; s < 3; ++s) totals[s] = r[6 + s];
+        for (int s = 0; s < 3; ++s) totals[s] = c->host_out[6 + s];
     }
     return LBMS_OK;
 }
@@ -630,12 +906,15 @@ lbms_status lbms_boundary_flux(lbms_ctx* c, double* inlet_flux, double* totals) 
 lbms_status lbms_get_info(const lbms_ctx* c, lbms_info* info) {
     if (!c || !info) return LBMS_EINVAL;
     std::memset(info, 0, sizeof(*info));
-    info->n_cells = c->N;
-    info->n_fluid = (int64_t)c->fluid_cell.size();
+    const CaseHost& c0 = c->cases[0];
+    for (const auto& cs : c->cases) {
+        info->n_cells += cs.N;
+        info->n_fluid += cs.nf;
+    }
     info->q = c->Q;
     info->precision = c->opt.precision;
-    info->dx_m = c->gas.dx;
-    info->dt_s = c->gas.dt;
+    info->dx_m = c0.dx;
+    info->dt_s = c0.dt;
     info->C_t = c->gas.C_t;
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) {
@@ -643,14 +922,17 @@ lbms_status lbms_get_info(const lbms_ctx* c, lbms_info* info) {
             info->D_lat[i * 3 + j] = c->gas.D_lat[i][j];
         }
     for (int s = 0; s < 3; ++s) {
-        info->q_lat[s] = c->L.q[s];
-        info->x_in[s] = c->x_in[s];
+        info->q_lat[s] = c0.q[s];
+        info->x_in[s] = c0.x_in[s];
     }
-    info->current_A_cm2 = c->current;
+    info->current_A_cm2 = c0.current;
     info->steps = c->steps;
     info->device_bytes = c->device_bytes;
     info->h2d_bytes = c->h2d;
     info->d2h_bytes = c->d2h;
+    info->n_cases = (int)c->cases.size();
+    info->tile_cells = kVariantCells[c->L.variant];
+    info->tile_min_blocks = kVariantMinBlocks[c->L.variant];
     return LBMS_OK;
 }
 

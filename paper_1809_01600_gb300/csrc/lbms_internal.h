@@ -8,33 +8,42 @@
 
 namespace lbms {
 
-constexpr int kRedSlots = 16;          // doubles per reduction result slot
-constexpr int kRedResidual = 0;        // slot of the residual sums
-constexpr int kRedBoundary = 1;        // slot of the boundary sums
-constexpr int kRedMaxBlocks = 1216;    // 152 SMs x 8 resident blocks of 256 threads
+constexpr int kCaseOutSlots = 16;      // doubles per case: residual sums (10) | boundary sums (6)
+
+// Tile shapes of the step kernel the autotuner chooses from:
+// (cells per block, minimum resident blocks per SM for the register budget).
+constexpr int kStepVariants = 3;
+constexpr int kVariantCells[kStepVariants] = {32, 32, 64};
+constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4};
 
 struct DevBuffers {
     void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]
-    void* X[2] = {nullptr, nullptr};   // mole fractions (double or double-float pairs), [3][S]
+    void* X[2] = {nullptr, nullptr};   // mole fractions (double or double-float blocks)
     double* snap = nullptr;            // residual snapshot, [3][S]
     int* nbr = nullptr;                // [S][nb_width]
-    int* rows = nullptr;               // [3][nrows]: x = 0, x = 1, x = nx-1 cell per row (-1 if solid)
-    double* red_partials = nullptr;    // [kRedMaxBlocks][kRedSlots]
-    unsigned int* red_counter = nullptr;  // one per slot
-    double* red_out = nullptr;         // [2][kRedSlots]
+    int* rows = nullptr;               // [3][total rows]: x = 0, x = 1, x = nx-1 cell of each row (-1 if solid)
+    int2* case_rows = nullptr;         // [cases]: first row, row count
+    void* cases = nullptr;             // [cases] CaseBC<XS> (inlet values, outlet flux, range)
+    int* blk_case[kStepVariants] = {nullptr, nullptr, nullptr};  // step-kernel block -> case
+    int2* segs = nullptr;              // [segments]: first cell, cell count (reduction segments)
+    int2* case_segs = nullptr;         // [cases]: first segment, segment count
+    double* partials = nullptr;        // [segments][10]
+    double* case_out = nullptr;        // [cases][10] residual sums, then [cases][6] boundary sums
     void* fields = nullptr;            // [3 + 3 dim][S] of tau and u (lazy), FP64 or FP32
 };
 
 struct Launch {
     int dim = 2;
     int precision = 1;                 // 0 = FP64, 1 = FP32, 2 = FP16 populations / FP32 compute
-    int64_t S = 0;                     // padded row stride (elements)
-    int nf = 0;                        // fluid cells
-    int nrows = 0;                     // ny * nz
+    int64_t S = 0;                     // padded row stride (elements), >= ncells
+    int ncells = 0;                    // end of the last case's range (index space of the kernels)
+    int n_cases = 1;
+    int total_rows = 0;
+    int n_segs = 0;
+    int nblk[kStepVariants] = {0, 0, 0};
+    int variant = 0;                   // chosen step-kernel tile shape
     int cur = 0;                       // lattice holding the latest post-collision state
     DevBuffers b;
-    double xin[3] = {0, 0, 0};
-    double q[3] = {0, 0, 0};
     double D12 = 1, D13 = 1, D23 = 1;  // lattice binary diffusivities
     double stoich[3] = {-1, 1, 0};     // nu_i of the electrode reaction (Eq. 38)
     double tau_min = 1.0, tau_max = 5.0;
@@ -42,15 +51,26 @@ struct Launch {
     int sm_count = 152;
 };
 
+// Host image of one case's boundary data; the launcher converts it to the
+// device CaseBC layout of the precision in use.
+struct CaseHostBC {
+    double xin[3];
+    double q[3];
+    int base;
+    int nf;
+};
+
 size_t pop_size(int precision);    // bytes per stored population
 size_t x_size(int precision);      // bytes per stored mole fraction
 size_t field_size(int precision);  // bytes per tau / u value of the fields kernel
-int residual_blocks(const Launch& L);
+size_t case_bc_size(int precision);
+void pack_case_bc(int precision, const CaseHostBC& h, void* dst);  // host-side CaseBC image
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st);
-cudaError_t launch_init(const Launch& L, cudaStream_t st);
+cudaError_t launch_step_variant(const Launch& L, int variant, cudaStream_t st);
+cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st);
 cudaError_t launch_fields(const Launch& L, cudaStream_t st);
-cudaError_t launch_residual(const Launch& L, int update, cudaStream_t st);
-cudaError_t launch_boundary(const Launch& L, cudaStream_t st);
+cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st);
+cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st);
 
 }  // namespace lbms

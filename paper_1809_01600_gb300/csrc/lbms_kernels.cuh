@@ -125,6 +125,19 @@ struct Xv<float> {
     }
 };
 
+// Per-case data of a batch.  Every case owns the fluid-index range
+// [base, base + nf), with base a multiple of kCaseAlign, so that no block of
+// the step kernel spans two cases.
+constexpr int kCaseAlign = 64;
+
+template <typename XS>
+struct CaseBC {
+    Xv<XS> xbc[3];                    // inlet mole fractions (Eq. 36), in the X format
+    typename Xv<XS>::T qout[3];       // outlet flux per node per step (Eq. 39)
+    int base;                         // first fluid index of the case
+    int nf;                           // fluid cells of the case
+};
+
 template <typename XS, typename P>
 struct StepParams {
     const P* __restrict__ hin;
@@ -132,10 +145,9 @@ struct StepParams {
     const XS* __restrict__ xin;
     XS* __restrict__ xout;
     const int* __restrict__ nbr;
+    const CaseBC<XS>* __restrict__ cases;
+    const int* __restrict__ blk_case;   // case of each block of W cells
     int64_t S;
-    int nf;
-    Xv<XS> xbc[3];                    // inlet mole fractions (Eq. 36), in the X format
-    typename Xv<XS>::T qout[3];       // outlet flux per node per step (Eq. 39)
     MsConst<typename Xv<XS>::T> c;
 };
 
@@ -236,8 +248,8 @@ __device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], co
 // of a warp walks consecutive cells of one species row.  The three threads of
 // a cell meet once, through shared memory, to exchange X and its gradient for
 // the coupling (which needs all species).
-template <class L, typename XS, typename P, int W>
-__global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> p) {
+template <class L, typename XS, typename P, int W, int MB>
+__global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P> p) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
     constexpr int Q = L::Q;
@@ -248,7 +260,10 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> 
     const int s = threadIdx.x / W;          // species of this thread
     const int c = threadIdx.x - s * W;      // cell slot in the block
     const int i = blockIdx.x * W + c;
-    const bool active = i < p.nf;
+    // Every thread of the grid runs, padding cells between cases included:
+    // their neighbour rows hold only NB_SOLID and their state stays zero, no
+    // real cell reads them, so no branch waits for the case lookup below.
+    const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
     const int64_t S = p.S;
     const int S32 = (int)S;      // Q * S < 2^31 (checked at create): 32-bit offsets in a species block
     const P* hs = p.hin + (int64_t)s * Q * S;
@@ -257,13 +272,13 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> 
     T d[Q];          // f_k(x) - w_k X_old(x) after streaming
     XV xo, xn;
     T dX = T(0);
-    if (active) {
+    {
         nb[0] = i;
         load_neighbours<L>(p.nbr, i, nb);
         xo = XV::own(p.xin, S, s, i);
         T dxs[Q];    // X(src) - X_old(x) for fluid sources, 0 otherwise
         constexpr T wx = T(weight_xplus<L>());
-        const T qs = s == 0 ? p.qout[0] : (s == 1 ? p.qout[1] : p.qout[2]);
+        const T qs = cb.qout[s];
         d[0] = Pop<T, P>::load(hs + i);
         dxs[0] = T(0);
         // Every link loads unconditionally (no branch between the gathers): a
@@ -282,7 +297,7 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> 
             dxs[k] = dx;
         }
         // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
-        const XV xb = s == 0 ? p.xbc[0] : (s == 1 ? p.xbc[1] : p.xbc[2]);
+        const XV xb = cb.xbc[s];
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
             if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
@@ -303,7 +318,6 @@ __global__ void __launch_bounds__(3 * W, 8) step_kernel(const StepParams<XS, P> 
         sX[s][c] = xn.value();
     }
     __syncthreads();
-    if (!active) return;
 
     T X[3], g[3][DIM];
 #pragma unroll
@@ -384,14 +398,15 @@ __global__ void fields_kernel(const XS* __restrict__ xcur, const XS* __restrict_
     }
 }
 
-// Equilibrium start (Eq. 29, f = w X): h = 0; the second X copy and the
-// residual snapshot take X (already in x0).
+// Equilibrium start (Eq. 29, f = w X) of cells [first, first + count): h = 0;
+// the second X copy and the residual snapshot take X (already in x0).
 template <class L, typename XS, typename P>
 __global__ void init_kernel(P* __restrict__ h, const XS* __restrict__ x0, XS* __restrict__ x1,
-                            double* __restrict__ snap, int64_t S, int nf) {
+                            double* __restrict__ snap, int64_t S, int first, int count) {
     using T = typename Xv<XS>::T;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const int i = first + j;
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
         const Xv<XS> v = Xv<XS>::own(x0, S, s, i);
@@ -491,23 +506,96 @@ __global__ void __launch_bounds__(256) residual_kernel(const XS* __restrict__ X,
     reduce_to_out<10>(acc, partials, counter, out);
 }
 
-// Boundary sums in FP64 over the ny*nz rows: out[0..2] = net flux toward +x
-// through the plane between x = 0 and x = 1, carried by the post-collision
-// populations w X + h of the last step; out[3..5] = sum of X over the outlet
-// column.
+// -------------------------------------------------------------------------
+// Per-case FP64 reductions of a batch, deterministic: a first kernel writes
+// one partial per segment (a run of at most kSegCells cells of one case),
+// a second sums each case's segments in order.
+constexpr int kSegCells = 1024;
+constexpr int kSegThreads = 256;
+
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&acc)[NV], double* __restrict__ dst) {
+    __shared__ double sm[kSegThreads / 32][NV];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double a = acc[v];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+        if (lane == 0) sm[warp][v] = a;
+    }
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            double a = lane < kSegThreads / 32 ? sm[lane][v] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) dst[v] = a;
+        }
+    }
+}
+
+// Residual partials of one segment (NV = 10: sum (X - snap)^2, sum X^2,
+// sum X per species, count of non-finite X); the snapshot takes X when
+// update != 0.
+template <typename XS>
+__global__ void __launch_bounds__(kSegThreads) seg_residual_kernel(const XS* __restrict__ X, double* __restrict__ snap,
+                                                                   int64_t S, const int2* __restrict__ segs, int update,
+                                                                   double* __restrict__ partials) {
+    const int2 sg = segs[blockIdx.x];   // (first cell, cell count)
+    double acc[10];
+#pragma unroll
+    for (int v = 0; v < 10; ++v) acc[v] = 0.0;
+    for (int j = threadIdx.x; j < sg.y; j += kSegThreads) {
+        const int i = sg.x + j;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const double x = Xv<XS>::own(X, S, s, i).to_double();
+            const double d = x - snap[s * S + i];
+            acc[s] += d * d;
+            acc[3 + s] += x * x;
+            acc[6 + s] += x;
+            if (!isfinite(x)) acc[9] += 1.0;
+            if (update) snap[s * S + i] = x;
+        }
+    }
+    block_sum<10>(acc, partials + (int64_t)blockIdx.x * 10);
+}
+
+// Sums the partials of each case's segments [first, first + count) in order.
+template <int NV>
+__global__ void seg_finalize_kernel(const double* __restrict__ partials, const int2* __restrict__ case_segs,
+                                    double* __restrict__ out) {
+    const int2 r = case_segs[blockIdx.x];
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int j = threadIdx.x; j < r.y; j += kSegThreads) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] += partials[(int64_t)(r.x + j) * NV + v];
+    }
+    block_sum<NV>(acc, out + (int64_t)blockIdx.x * NV);
+}
+
+// Boundary sums of each case (one block per case, rows [first, first + count)
+// of the concatenated row lists): out[0..2] = net flux toward +x through the
+// plane between x = 0 and x = 1, carried by the post-collision populations
+// w X + h of the last step; out[3..5] = sum of X over the outlet column.
 template <class L, typename XS, typename P>
-__global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, const XS* __restrict__ X,
-                                                       const int* __restrict__ nbr, int64_t S,
-                                                       const int* __restrict__ row_x0, const int* __restrict__ row_x1,
-                                                       const int* __restrict__ row_out, int nrows,
-                                                       double* __restrict__ partials, unsigned int* __restrict__ counter,
-                                                       double* __restrict__ out) {
+__global__ void __launch_bounds__(kSegThreads) case_boundary_kernel(
+    const P* __restrict__ h, const XS* __restrict__ X, const int* __restrict__ nbr, int64_t S,
+    const int* __restrict__ row_x0, const int* __restrict__ row_x1, const int* __restrict__ row_out,
+    const int2* __restrict__ case_rows, double* __restrict__ out) {
     using T = typename Xv<XS>::T;
     constexpr int Q = L::Q;
+    const int2 rr = case_rows[blockIdx.x];
     double acc[6];
 #pragma unroll
     for (int v = 0; v < 6; ++v) acc[v] = 0.0;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nrows; r += gridDim.x * blockDim.x) {
+    for (int j = threadIdx.x; j < rr.y; j += kSegThreads) {
+        const int r = rr.x + j;
         const int i0 = row_x0[r];
         const int i1 = row_x1[r];
         const int io = row_out[r];
@@ -537,7 +625,7 @@ __global__ void __launch_bounds__(256) boundary_kernel(const P* __restrict__ h, 
             for (int s = 0; s < 3; ++s) acc[3 + s] += Xv<XS>::own(X, S, s, io).to_double();
         }
     }
-    reduce_to_out<6>(acc, partials, counter, out);
+    block_sum<6>(acc, out + (int64_t)blockIdx.x * 6);
 }
 
 }  // namespace lbms

@@ -1,8 +1,10 @@
 // Kernel instantiations and launch wrappers: D2Q9 / D3Q19 x
-//   FP64   (X double,           h double)
+//   FP64   (X double,                          h double)
 //   FP32   (X double-float pair in FP32 words, h float)
 //   FP16   (X double-float pair in FP32 words, h half, FP32 arithmetic)
+// and the step-kernel tile shapes of kVariantCells / kVariantMinBlocks.
 #include <algorithm>
+#include <cstring>
 
 #include "lbms_internal.h"
 #include "lbms_kernels.cuh"
@@ -12,7 +14,6 @@ namespace lbms {
 namespace {
 
 constexpr int kBlock = 256;
-constexpr int kCells = 32;     // cells per block of the step kernel (3 threads per cell)
 
 template <typename T>
 MsConst<T> make_const(const Launch& L) {
@@ -46,62 +47,83 @@ inline void to_x(double v, Xv<float>& out) {
     out.lo = (float)(v - (double)out.hi);
 }
 
-template <class Lat, typename XT, typename P>
-cudaError_t step_t(const Launch& L, cudaStream_t st) {
-    using T = typename Xv<XT>::T;
-    StepParams<XT, P> p;
+template <typename XS>
+void pack_t(const CaseHostBC& h, void* dst) {
+    CaseBC<XS> c;
+    std::memset(&c, 0, sizeof(c));
+    for (int s = 0; s < 3; ++s) {
+        to_x(h.xin[s], c.xbc[s]);
+        c.qout[s] = typename Xv<XS>::T(h.q[s]);
+    }
+    c.base = h.base;
+    c.nf = h.nf;
+    std::memcpy(dst, &c, sizeof(c));
+}
+
+template <class Lat, typename XS, typename P, int W, int MB>
+cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
+    using T = typename Xv<XS>::T;
+    StepParams<XS, P> p;
     p.hin = static_cast<const P*>(L.b.f[L.cur]);
     p.hout = static_cast<P*>(L.b.f[L.cur ^ 1]);
-    p.xin = static_cast<const XT*>(L.b.X[L.cur]);
-    p.xout = static_cast<XT*>(L.b.X[L.cur ^ 1]);
+    p.xin = static_cast<const XS*>(L.b.X[L.cur]);
+    p.xout = static_cast<XS*>(L.b.X[L.cur ^ 1]);
     p.nbr = L.b.nbr;
+    p.cases = static_cast<const CaseBC<XS>*>(L.b.cases);
+    p.blk_case = L.b.blk_case[variant];
     p.S = L.S;
-    p.nf = L.nf;
-    for (int s = 0; s < 3; ++s) {
-        to_x(L.xin[s], p.xbc[s]);
-        p.qout[s] = T(L.q[s]);
-    }
     p.c = make_const<T>(L);
-    const int grid = (L.nf + kCells - 1) / kCells;
-    step_kernel<Lat, XT, P, kCells><<<grid, 3 * kCells, 0, st>>>(p);
+    step_kernel<Lat, XS, P, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
     return cudaGetLastError();
 }
 
-template <class Lat, typename XT, typename P>
-cudaError_t init_t(const Launch& L, cudaStream_t st) {
-    const int grid = (L.nf + kBlock - 1) / kBlock;
-    init_kernel<Lat, XT, P><<<grid, kBlock, 0, st>>>(static_cast<P*>(L.b.f[L.cur]),
-                                                     static_cast<const XT*>(L.b.X[L.cur]),
-                                                     static_cast<XT*>(L.b.X[L.cur ^ 1]), L.b.snap, L.S, L.nf);
+template <class Lat, typename XS, typename P>
+cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
+    static_assert(kStepVariants == 3, "variant table");
+    if (variant == 0) return step_w<Lat, XS, P, kVariantCells[0], kVariantMinBlocks[0]>(L, 0, st);
+    if (variant == 1) return step_w<Lat, XS, P, kVariantCells[1], kVariantMinBlocks[1]>(L, 1, st);
+    return step_w<Lat, XS, P, kVariantCells[2], kVariantMinBlocks[2]>(L, 2, st);
+}
+
+template <class Lat, typename XS, typename P>
+cudaError_t init_t(const Launch& L, int first, int count, cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int grid = (count + kBlock - 1) / kBlock;
+    init_kernel<Lat, XS, P><<<grid, kBlock, 0, st>>>(static_cast<P*>(L.b.f[L.cur]),
+                                                     static_cast<const XS*>(L.b.X[L.cur]),
+                                                     static_cast<XS*>(L.b.X[L.cur ^ 1]), L.b.snap, L.S, first, count);
     return cudaGetLastError();
 }
 
-template <class Lat, typename XT, typename P>
+template <class Lat, typename XS, typename P>
 cudaError_t fields_t(const Launch& L, cudaStream_t st) {
-    using T = typename Xv<XT>::T;
-    const int grid = (L.nf + kBlock - 1) / kBlock;
+    using T = typename Xv<XS>::T;
+    const int grid = (L.ncells + kBlock - 1) / kBlock;
     T* base = static_cast<T*>(L.b.fields);
-    fields_kernel<Lat, XT><<<grid, kBlock, 0, st>>>(static_cast<const XT*>(L.b.X[L.cur]),
-                                                    static_cast<const XT*>(L.b.X[L.cur ^ 1]), L.b.nbr, L.S, L.nf,
-                                                    make_const<T>(L), base, base + 3 * L.S);
+    fields_kernel<Lat, XS><<<grid, kBlock, 0, st>>>(static_cast<const XS*>(L.b.X[L.cur]),
+                                                    static_cast<const XS*>(L.b.X[L.cur ^ 1]), L.b.nbr, L.S,
+                                                    L.ncells, make_const<T>(L), base, base + 3 * L.S);
     return cudaGetLastError();
 }
 
-template <typename XT>
+template <typename XS>
 cudaError_t residual_t(const Launch& L, int update, cudaStream_t st) {
-    residual_kernel<XT><<<residual_blocks(L), kBlock, 0, st>>>(
-        static_cast<const XT*>(L.b.X[L.cur]), L.b.snap, L.S, L.nf, update, L.b.red_partials,
-        L.b.red_counter + kRedResidual, L.b.red_out + kRedResidual * kRedSlots);
+    seg_residual_kernel<XS><<<L.n_segs, kSegThreads, 0, st>>>(static_cast<const XS*>(L.b.X[L.cur]), L.b.snap, L.S,
+                                                              L.b.segs, update, L.b.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // per-case sums land in case_out[c * 10 + v]
+    seg_finalize_kernel<10><<<L.n_cases, kSegThreads, 0, st>>>(L.b.partials, L.b.case_segs, L.b.case_out);
     return cudaGetLastError();
 }
 
-template <class Lat, typename XT, typename P>
+template <class Lat, typename XS, typename P>
 cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
-    const int blocks = std::max(1, std::min((L.nrows + kBlock - 1) / kBlock, kRedMaxBlocks / 2));
-    boundary_kernel<Lat, XT, P><<<blocks, kBlock, 0, st>>>(
-        static_cast<const P*>(L.b.f[L.cur]), static_cast<const XT*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
-        L.b.rows + L.nrows, L.b.rows + 2 * L.nrows, L.nrows, L.b.red_partials + kRedMaxBlocks * kRedSlots / 2,
-        L.b.red_counter + kRedBoundary, L.b.red_out + kRedBoundary * kRedSlots);
+    // per-case sums land in case_out[n_cases * 10 + c * 6 + v]
+    case_boundary_kernel<Lat, XS, P><<<L.n_cases, kSegThreads, 0, st>>>(
+        static_cast<const P*>(L.b.f[L.cur]), static_cast<const XS*>(L.b.X[L.cur]), L.b.nbr, L.S, L.b.rows,
+        L.b.rows + L.total_rows, L.b.rows + 2 * L.total_rows, L.b.case_rows,
+        L.b.case_out + (int64_t)L.n_cases * 10);
     return cudaGetLastError();
 }
 
@@ -110,30 +132,38 @@ cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
 size_t pop_size(int precision) { return precision == 0 ? sizeof(double) : (precision == 1 ? sizeof(float) : 2); }
 size_t x_size(int precision) { return precision == 0 ? sizeof(double) : 2 * sizeof(float); }
 size_t field_size(int precision) { return precision == 0 ? sizeof(double) : sizeof(float); }
+size_t case_bc_size(int precision) { return precision == 0 ? sizeof(CaseBC<double>) : sizeof(CaseBC<float>); }
 
-int residual_blocks(const Launch& L) {
-    const int want = (L.nf + kBlock - 1) / kBlock;
-    return std::max(1, std::min(want, std::min(kRedMaxBlocks / 2, 4 * L.sm_count)));
+void pack_case_bc(int precision, const CaseHostBC& h, void* dst) {
+    if (precision == 0)
+        pack_t<double>(h, dst);
+    else
+        pack_t<float>(h, dst);
 }
 
 #define LBMS_DISPATCH(FN, ...)                                                              \
     do {                                                                                    \
         if (L.dim == 2) {                                                                   \
             if (L.precision == 0) return FN<D2Q9, double, double>(__VA_ARGS__);             \
-            if (L.precision == 1) return FN<D2Q9, float, float>(__VA_ARGS__);              \
-            return FN<D2Q9, float, __half>(__VA_ARGS__);                                   \
+            if (L.precision == 1) return FN<D2Q9, float, float>(__VA_ARGS__);               \
+            return FN<D2Q9, float, __half>(__VA_ARGS__);                                    \
         }                                                                                   \
         if (L.precision == 0) return FN<D3Q19, double, double>(__VA_ARGS__);                \
-        if (L.precision == 1) return FN<D3Q19, float, float>(__VA_ARGS__);                 \
-        return FN<D3Q19, float, __half>(__VA_ARGS__);                                      \
+        if (L.precision == 1) return FN<D3Q19, float, float>(__VA_ARGS__);                  \
+        return FN<D3Q19, float, __half>(__VA_ARGS__);                                       \
     } while (0)
 
-cudaError_t launch_step(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(step_t, L, st); }
-cudaError_t launch_init(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(init_t, L, st); }
+cudaError_t launch_step_variant(const Launch& L, int variant, cudaStream_t st) {
+    LBMS_DISPATCH(step_t, L, variant, st);
+}
+cudaError_t launch_step(const Launch& L, cudaStream_t st) { return launch_step_variant(L, L.variant, st); }
+cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st) {
+    LBMS_DISPATCH(init_t, L, first, count, st);
+}
 cudaError_t launch_fields(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(fields_t, L, st); }
-cudaError_t launch_boundary(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(boundary_t, L, st); }
+cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(boundary_t, L, st); }
 
-cudaError_t launch_residual(const Launch& L, int update, cudaStream_t st) {
+cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st) {
     return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float>(L, update, st);
 }
 

@@ -27,7 +27,9 @@ STATUS_NAMES = {0: "LBMS_OK", 1: "LBMS_EINVAL", 2: "LBMS_ENOMEM", 3: "LBMS_ECUDA
 EXPORTS = ("lbms_default_options", "lbms_create", "lbms_set_bc", "lbms_set_fields", "lbms_step",
            "lbms_residual", "lbms_run_to_residual", "lbms_get_fields", "lbms_overpotential",
            "lbms_boundary_flux", "lbms_get_info", "lbms_synchronize", "lbms_destroy",
-           "lbms_last_error", "lbms_status_string", "lbms_residual_sums_noalloc")
+           "lbms_last_error", "lbms_status_string", "lbms_residual_sums_noalloc",
+           "lbms_create_batch", "lbms_batch_set_bc", "lbms_batch_set_fields", "lbms_batch_residuals",
+           "lbms_batch_run_to_residual", "lbms_batch_get_fields", "lbms_batch_overpotentials")
 
 
 class LbmsError(RuntimeError):
@@ -71,7 +73,8 @@ class Info(C.Structure):
                 ("q_lat", C.c_double * 3), ("x_in", C.c_double * 3),
                 ("current_A_cm2", C.c_double), ("steps", C.c_int64),
                 ("device_bytes", C.c_size_t), ("h2d_bytes", C.c_uint64),
-                ("d2h_bytes", C.c_uint64)]
+                ("d2h_bytes", C.c_uint64), ("n_cases", C.c_int), ("tile_cells", C.c_int),
+                ("tile_min_blocks", C.c_int)]
 
 
 _lib = None
@@ -107,6 +110,15 @@ def load(build_if_needed: bool = True):
         "lbms_last_error": (C.c_char_p, [P]),
         "lbms_status_string": (C.c_char_p, [C.c_int]),
         "lbms_residual_sums_noalloc": (st, [P, P, I64, C.c_int, P, P]),
+        "lbms_create_batch": (st, [C.c_int, C.POINTER(Geometry), C.POINTER(Species),
+                                   C.POINTER(Diffusivities), C.c_double, C.c_double,
+                                   C.POINTER(Options), C.POINTER(P)]),
+        "lbms_batch_set_bc": (st, [P, C.c_int, D, C.c_double]),
+        "lbms_batch_set_fields": (st, [P, C.c_int, D]),
+        "lbms_batch_residuals": (st, [P, C.c_int, D]),
+        "lbms_batch_run_to_residual": (st, [P, C.c_double, I64, C.POINTER(I64), C.POINTER(I64), D]),
+        "lbms_batch_get_fields": (st, [P, C.c_int, D, D, D]),
+        "lbms_batch_overpotentials": (st, [P, D, D]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -120,31 +132,14 @@ def _dptr(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-class Solver:
-    """One solver instance on the current CUDA device (a handle of the C ABI).
+class _Handle:
+    """Argument marshalling shared by Solver and Batch."""
 
-    ``solid`` is a bool array [z, y, x] (or [y, x] in 2-D), True = solid.
-    """
-
-    def __init__(self, solid, dim=None, length_x=2e-3, periodic_x=False, *,
-                 molar_mass=(2.016, 18.015, 39.948), fuller_volume=(6.12, 13.1, 16.2),
-                 stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
-                 eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
-                 tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
-                 torch_allocator=True):
+    def _setup(self, molar_mass, fuller_volume, stoich, electrons, D_binary, pore_diameter,
+               eps_over_tau, precision, coupling, tau_min, tau_max, dt, check_every, stream,
+               torch_allocator):
         lib = load()
         self._lib = lib
-        solid = np.asarray(solid, dtype=bool)
-        if solid.ndim == 2:
-            solid = solid[None]
-        nz, ny, nx = solid.shape
-        if dim is None:
-            dim = 2 if nz == 1 else 3
-        self.shape = solid.shape
-        self.dim = dim
-        self.N = solid.size
-        mask = np.ascontiguousarray(solid.astype(np.uint8))
-        g = Geometry(dim, nx, ny, nz, mask.ctypes.data, float(length_x), int(bool(periodic_x)))
         self._mm = np.ascontiguousarray(molar_mass, dtype=np.float64)
         self._fv = np.ascontiguousarray(fuller_volume, dtype=np.float64)
         self._nu = np.ascontiguousarray(stoich, dtype=np.int32)
@@ -187,19 +182,184 @@ class Solver:
                 pass
         o.stream = stream or None
         self.stream = stream or 0
-        h = C.c_void_p()
-        s = lib.lbms_create(C.byref(g), C.byref(sp), C.byref(df), float(T), float(p), C.byref(o),
-                            C.byref(h))
-        if s != LBMS_OK:
-            raise LbmsError(s, lib.lbms_last_error(None).decode())
-        self._h = h
         self._opts = o
+        return sp, df, o
 
-    # -------------------------------------------------------------- helpers
+    @staticmethod
+    def _geometry(solid, dim, length_x, periodic_x):
+        solid = np.asarray(solid, dtype=bool)
+        if solid.ndim == 2:
+            solid = solid[None]
+        nz, ny, nx = solid.shape
+        if dim is None:
+            dim = 2 if nz == 1 else 3
+        mask = np.ascontiguousarray(solid.astype(np.uint8))
+        g = Geometry(dim, nx, ny, nz, mask.ctypes.data, float(length_x), int(bool(periodic_x)))
+        return g, mask, solid.shape, dim
+
     def _check(self, s):
         if s != LBMS_OK:
             raise LbmsError(s, self._lib.lbms_last_error(self._h).decode())
 
+    def step(self, n=1):
+        self._check(self._lib.lbms_step(self._h, int(n)))
+
+    def info(self):
+        i = Info()
+        self._check(self._lib.lbms_get_info(self._h, C.byref(i)))
+        return i
+
+    def synchronize(self):
+        self._check(self._lib.lbms_synchronize(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbms_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+_GAS_DEFAULTS = dict(molar_mass=(2.016, 18.015, 39.948), fuller_volume=(6.12, 13.1, 16.2),
+                     stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
+                     eps_over_tau=1.0)
+
+
+def _case_gas(case):
+    g = case.gas
+    return dict(molar_mass=g.molar_mass, fuller_volume=g.fuller_volume, stoich=g.stoich,
+                electrons=g.electrons, D_binary=g.D_binary, pore_diameter=g.pore_diameter,
+                eps_over_tau=g.eps_over_tau, T=g.T, p=g.p)
+
+
+class Batch(_Handle):
+    """Several independent anodes stepped by one kernel launch per step.
+
+    ``solids`` is a list of bool arrays [z, y, x] (all 2-D or all 3-D);
+    ``length_x`` and ``periodic_x`` are scalars or per-case lists.
+    """
+
+    def __init__(self, solids, dim=None, length_x=2e-3, periodic_x=False, *, T=1073.0, p=101325.0,
+                 precision="fp32", coupling="ms", tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100,
+                 stream=None, torch_allocator=True, **gas):
+        g = dict(_GAS_DEFAULTS)
+        g.update(gas)
+        sp, df, o = self._setup(g["molar_mass"], g["fuller_volume"], g["stoich"], g["electrons"],
+                                g["D_binary"], g["pore_diameter"], g["eps_over_tau"], precision,
+                                coupling, tau_min, tau_max, dt, check_every, stream, torch_allocator)
+        n = len(solids)
+        lx = list(length_x) if np.ndim(length_x) else [length_x] * n
+        px = list(periodic_x) if np.ndim(periodic_x) else [periodic_x] * n
+        geoms = (Geometry * n)()
+        self._masks, self.shapes = [], []
+        for k in range(n):
+            gk, mask, shape, d = self._geometry(solids[k], dim, lx[k], px[k])
+            geoms[k] = gk
+            self._masks.append(mask)
+            self.shapes.append(shape)
+            self.dim = d
+        self.n = n
+        h = C.c_void_p()
+        s = self._lib.lbms_create_batch(n, geoms, C.byref(sp), C.byref(df), float(T), float(p),
+                                        C.byref(o), C.byref(h))
+        if s != LBMS_OK:
+            raise LbmsError(s, self._lib.lbms_last_error(None).decode())
+        self._h = h
+
+    @classmethod
+    def from_cases(cls, cases, **kw):
+        """Builds a batch from workload descriptions sharing the same gas."""
+        args = dict(dim=cases[0].dim, length_x=[c.length_x for c in cases],
+                    periodic_x=[c.periodic_x for c in cases])
+        args.update(_case_gas(cases[0]))
+        args.update(kw)
+        b = cls([c.solid for c in cases], **args)
+        return b
+
+    def set_bc(self, x_in, current_A_cm2, case=None):
+        x = np.ascontiguousarray(x_in, dtype=np.float64)
+        if case is None:
+            self._check(self._lib.lbms_set_bc(self._h, _dptr(x), float(current_A_cm2)))
+        else:
+            self._check(self._lib.lbms_batch_set_bc(self._h, int(case), _dptr(x), float(current_A_cm2)))
+
+    def set_fields(self, case, X):
+        n = int(np.prod(self.shapes[case]))
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(3 * n)
+        self._check(self._lib.lbms_batch_set_fields(self._h, int(case), _dptr(X)))
+
+    def residuals(self, K):
+        r = np.empty(self.n)
+        self._check(self._lib.lbms_batch_residuals(self._h, int(K), _dptr(r)))
+        return r
+
+    def run_to_residual(self, tol, max_steps, raise_on_fail=True):
+        n = C.c_int64()
+        steps = np.empty(self.n, dtype=np.int64)
+        r = np.empty(self.n)
+        s = self._lib.lbms_batch_run_to_residual(self._h, float(tol), int(max_steps), C.byref(n),
+                                                 steps.ctypes.data_as(C.POINTER(C.c_int64)), _dptr(r))
+        if raise_on_fail:
+            self._check(s)
+        return n.value, steps, r, s
+
+    def fields(self, case, u=False, tau=False):
+        shape = self.shapes[case]
+        X = np.empty((3,) + shape)
+        U = np.empty((3, self.dim) + shape) if u else None
+        T = np.empty((3,) + shape) if tau else None
+        self._check(self._lib.lbms_batch_get_fields(self._h, int(case), _dptr(X),
+                                                    _dptr(U) if u else None, _dptr(T) if tau else None))
+        out = [X] + ([U] if u else []) + ([T] if tau else [])
+        return out[0] if len(out) == 1 else tuple(out)
+
+    def overpotentials(self, raise_on_fail=True):
+        eta = np.empty(self.n)
+        xo = np.empty((self.n, 3))
+        s = self._lib.lbms_batch_overpotentials(self._h, _dptr(eta), _dptr(xo))
+        if raise_on_fail:
+            self._check(s)
+        return eta, xo
+
+
+class Solver(_Handle):
+    """One solver instance on the current CUDA device (a handle of the C ABI).
+
+    ``solid`` is a bool array [z, y, x] (or [y, x] in 2-D), True = solid.
+    """
+
+    def __init__(self, solid, dim=None, length_x=2e-3, periodic_x=False, *,
+                 molar_mass=(2.016, 18.015, 39.948), fuller_volume=(6.12, 13.1, 16.2),
+                 stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
+                 eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
+                 tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
+                 torch_allocator=True):
+        sp, df, o = self._setup(molar_mass, fuller_volume, stoich, electrons, D_binary,
+                                pore_diameter, eps_over_tau, precision, coupling, tau_min, tau_max,
+                                dt, check_every, stream, torch_allocator)
+        g, mask, shape, dim = self._geometry(solid, dim, length_x, periodic_x)
+        self._mask = mask
+        self.shape = shape
+        self.dim = dim
+        self.N = int(np.prod(shape))
+        h = C.c_void_p()
+        s = self._lib.lbms_create(C.byref(g), C.byref(sp), C.byref(df), float(T), float(p),
+                                  C.byref(o), C.byref(h))
+        if s != LBMS_OK:
+            raise LbmsError(s, self._lib.lbms_last_error(None).decode())
+        self._h = h
+
+    # -------------------------------------------------------------- helpers
     @classmethod
     def from_case(cls, case, **kw):
         """Builds a solver from a workload description (duck-typed)."""
@@ -219,9 +379,6 @@ class Solver:
     def set_fields(self, X):
         X = np.ascontiguousarray(X, dtype=np.float64).reshape(3 * self.N)
         self._check(self._lib.lbms_set_fields(self._h, _dptr(X)))
-
-    def step(self, n=1):
-        self._check(self._lib.lbms_step(self._h, int(n)))
 
     def residual(self, K):
         r = C.c_double()
@@ -262,27 +419,3 @@ class Solver:
         self._check(self._lib.lbms_boundary_flux(self._h, _dptr(fl), _dptr(tot)))
         return fl, tot
 
-    def info(self):
-        i = Info()
-        self._check(self._lib.lbms_get_info(self._h, C.byref(i)))
-        return i
-
-    def synchronize(self):
-        self._check(self._lib.lbms_synchronize(self._h))
-
-    def close(self):
-        if getattr(self, "_h", None):
-            self._lib.lbms_destroy(self._h)
-            self._h = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-    def __enter__(self):
-        return self
-
-    def __exit__(self, *a):
-        self.close()

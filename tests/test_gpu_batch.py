@@ -1,0 +1,88 @@
+"""Batched stepping: every case of a batch evolves as the same case in a
+handle of its own, to rounding (the autotuner may pick another tile shape,
+whose instantiation can contract floating-point operations differently);
+per-case residuals, convergence counts and overpotentials."""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from workloads import cases
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_01600_gb300 import lbms
+    lbms.load()
+    return lbms
+
+
+def _cases_2d():
+    shapes = [(24, 40), (17, 33), (40, 64)]
+    out = []
+    for k, sh in enumerate(shapes):
+        c = cases.porous(sh, radius=3, porosity=0.55, seed=40 + k)
+        out.append(c)
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-7), ("fp16", 1e-6)])
+def test_batch_equals_single_cases_2d(L, precision, tol):
+    cs = _cases_2d()
+    ops = [(0.5, (0.5, 0.1, 0.4)), (1.5, (0.3, 0.075, 0.625)), (1.0, (0.6, 0.15, 0.25))]
+    b = L.Batch.from_cases(cs, precision=precision)
+    for k, (I, x) in enumerate(ops):
+        b.set_bc(x, I, case=k)
+    info = b.info()
+    assert info.n_cases == 3 and info.tile_cells in (32, 64)
+    b.step(137)
+    eta_b, xo_b = b.overpotentials()
+    for k, (c, (I, x)) in enumerate(zip(cs, ops)):
+        s = L.Solver.from_case(c, precision=precision)
+        s.set_bc(x, I)
+        s.step(137)
+        Xs = s.fields()
+        Xb = b.fields(k)
+        assert np.abs(Xs - Xb).max() <= tol, f"case {k}: {np.abs(Xs - Xb).max():.3e}"
+        eta, xo = s.overpotential()
+        assert eta_b[k] == pytest.approx(eta, rel=max(tol, 1e-12) * 100, abs=1e-15)
+        s.close()
+
+
+def test_batch_3d_matches_oracle_and_residuals(L):
+    cs = [cases.porous((10, 12, 20), radius=2, porosity=0.5, seed=51),
+          cases.porous((8, 8, 16), radius=2, porosity=0.6, seed=52)]
+    b = L.Batch.from_cases(cs, precision="fp64")
+    b.set_bc((0.5, 0.1, 0.4), 1.0, case=0)
+    b.set_bc((0.4, 0.1, 0.5), 2.0, case=1)
+    b.residuals(1)
+    b.step(50)
+    r = b.residuals(50)
+    assert r.shape == (2,) and np.all(r > 0)
+    o = Oracle(cs[1].with_(current_A_cm2=2.0, x_in=(0.4, 0.1, 0.5)))
+    o.step(50)
+    f = ~cs[1].solid
+    assert np.abs(b.fields(1) - o.X)[:, f].max() <= 1e-11
+
+
+def test_batch_run_to_residual_reports_each_case(L):
+    small = cases.porous((8, 12), radius=2, porosity=0.6, seed=61)
+    large = cases.porous((16, 48), radius=2, porosity=0.6, seed=62)
+    b = L.Batch.from_cases([small, large], precision="fp64")
+    b.set_bc((0.5, 0.1, 0.4), 1.0)
+    n, steps, r, st = b.run_to_residual(1e-9, 400000)
+    assert st == L.LBMS_OK
+    assert 0 < steps[0] < steps[1] <= n
+    assert np.all(r <= 1e-9)
+
+
+def test_batch_rejects_mixed_dims(L):
+    a = cases.porous((8, 12), radius=2, porosity=0.6, seed=61)
+    c = cases.porous((8, 8, 12), radius=2, porosity=0.6, seed=63)
+    with pytest.raises(L.LbmsError) as e:
+        L.Batch([a.solid, c.solid], dim=None)
+    assert e.value.status == L.LBMS_EINVAL

@@ -124,3 +124,43 @@ def gaussian_pulse(shape, axis: int, sigma0: float, amplitude: float,
     X[1] = background[1] - g
     X[2] = background[2]
     return X
+
+
+def sweep_structures(n2d: int, n3d: int, seed0: int = 100, scale: float = 1.0):
+    """Seeded microstructures in the style of the uneven-size sweep: 2-D
+    grids from 128x128 to 1024x512, 3-D cubes from 64^3 to 160^3 (sizes
+    times ``scale``), radius 2-6 cells, porosity uniform in [0.30, 0.55] in
+    3-D and in [0.42, 0.55] in 2-D, where the pore space of overlapping disks
+    stops percolating near 0.32 and long strips rarely percolate below 0.4.
+    Returns a list of Cases with default boundary data."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    out = []
+    for k in range(n2d + n3d):
+        seed = seed0 + k
+        por = float(rng.uniform(0.30, 0.55))
+        if k < n2d:
+            por = 0.42 + (por - 0.30) * (0.55 - 0.42) / 0.25
+        rad = int(rng.integers(2, 7))
+        if k < n2d:
+            nx = int(round(rng.uniform(128, 1024) * scale / 8)) * 8
+            ny = int(round(rng.uniform(128, 512) * scale / 8)) * 8
+            shape = (max(ny, 16), max(nx, 16))
+        else:
+            n = int(round(rng.uniform(64, 160) * scale / 8)) * 8
+            shape = (max(n, 16),) * 3
+        out.append(porous(shape, radius=rad, porosity=por, seed=seed,
+                          name=f"sweep{k}_{'x'.join(map(str, shape[::-1]))}_eps{por:.2f}_r{rad}"))
+    return out
+
+
+def sweep_operating_points(n: int = 8, seed0: int = 7):
+    """n (current A/cm2, inlet composition) pairs: currents evenly spread in
+    [0, 2], inlet H2 fraction drawn in [0.2, 0.8] at H2:H2O = 4:1 with Ar the
+    balance (Section 4.1)."""
+    rng = np.random.Generator(np.random.PCG64(seed0))
+    pts = []
+    for k in range(n):
+        I = 2.0 * k / max(n - 1, 1)
+        xh = float(rng.uniform(0.2, 0.8))
+        pts.append((I, (xh, xh / 4.0, 1.0 - 1.25 * xh)))
+    return pts
