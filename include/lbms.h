@@ -89,6 +89,12 @@ typedef struct {
  *  tau_min, tau_max  clamp of Eq. 25 [1, 5]
  *  dt_s       time step; 0 picks dt = dx^2 / (6 min D_ij,eff) [0]
  *  check_every residual interval K of run_to_residual [100]
+ *  extrapolate_every  W > 0: run_to_residual extrapolates the slowest decay
+ *             mode every W steps (Aitken: with rho the ratio of successive
+ *             W-step changes of X, X += rho / (1 - rho) * (last change) when
+ *             two successive ratios agree within 2 % and 0.05 < rho < 0.98).
+ *             The fixed point is unchanged; only the approach is shortened.
+ *             0 = off [0]
  *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
  *  alloc/free device allocator callbacks (e.g. a framework's caching
  *             allocator); NULL = cudaMalloc/cudaFree [NULL] */
@@ -98,6 +104,7 @@ typedef struct {
     double tau_min, tau_max;
     double dt_s;
     int check_every;
+    int extrapolate_every;
     void *stream;
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);

@@ -452,6 +452,62 @@ lbms_status overpotential_of(lbms_ctx* c, int k, double* eta, double* xo_out) {
 
 bool bad_case(const lbms_ctx* c, int k) { return !c || k < 0 || k >= (int)c->cases.size(); }
 
+// Aitken extrapolation of the slowest decay mode, per case (see the
+// extrapolate_every option).  norm_prev / rho_prev hold each case's last
+// W-step change and ratio (negative: none yet).
+struct Extrapolator {
+    std::vector<double> norm_prev, rho_prev, coef;
+    int64_t since = 0;
+};
+
+lbms_status extrap_begin(lbms_ctx* c, Extrapolator& ex) {
+    const int n = c->L.n_cases;
+    if (!c->L.b.extrap) {
+        c->L.b.extrap = static_cast<double*>(dev_alloc(c, (size_t)3 * c->L.S * sizeof(double)));
+        if (!c->L.b.extrap) return fail(c, LBMS_ENOMEM, "extrapolation snapshot");
+        CK(cudaMemsetAsync(c->L.b.extrap, 0, (size_t)3 * c->L.S * sizeof(double), c->stream), "extrapolation init");
+    }
+    ex.norm_prev.assign(n, -1.0);
+    ex.rho_prev.assign(n, -1.0);
+    ex.coef.assign(n, 0.0);
+    ex.since = 0;
+    // E = X (coefficient 0 leaves X alone)
+    CK(cudaMemcpyAsync(c->L.b.coef, ex.coef.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "coef");
+    CK(launch_extrapolate(c->L, c->stream), "extrapolation kernel");
+    return LBMS_OK;
+}
+
+lbms_status extrap_check(lbms_ctx* c, Extrapolator& ex) {
+    const int n = c->L.n_cases;
+    CK(launch_case_extrap_norms(c->L, c->stream), "extrapolation norms");
+    lbms_status st = read_case_out(c, 0, (size_t)n * 10);
+    if (st != LBMS_OK) return st;
+    for (int k = 0; k < n; ++k) {
+        const double* o = c->host_out + (size_t)k * 10;
+        const double nrm = std::sqrt(o[0] + o[1] + o[2]);
+        double cf = 0.0;
+        if (ex.norm_prev[k] > 0.0 && std::isfinite(nrm)) {
+            const double rho = nrm / ex.norm_prev[k];
+            if (ex.rho_prev[k] > 0.0 && std::fabs(rho - ex.rho_prev[k]) <= 0.02 * rho && rho > 0.05 && rho < 0.98) {
+                cf = rho / (1.0 - rho);
+                ex.norm_prev[k] = -1.0;   // the jump breaks the geometric sequence
+                ex.rho_prev[k] = -1.0;
+            } else {
+                ex.rho_prev[k] = rho;
+                ex.norm_prev[k] = nrm;
+            }
+        } else {
+            ex.norm_prev[k] = nrm;
+        }
+        ex.coef[k] = cf;
+    }
+    CK(cudaMemcpyAsync(c->L.b.coef, ex.coef.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "coef");
+    c->h2d += n * sizeof(double);
+    CK(launch_extrapolate(c->L, c->stream), "extrapolation kernel");
+    ex.since = 0;
+    return LBMS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -503,6 +559,7 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     else
         lbms_default_options(&c->opt);
     if (c->opt.check_every <= 0) c->opt.check_every = 100;
+    if (c->opt.extrapolate_every < 0) c->opt.extrapolate_every = 0;
     if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
     if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
@@ -601,10 +658,14 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
 
     // reduction segments and block -> case tables
     std::vector<int2> segs, case_segs(n_cases), case_rows(n_cases);
+    std::vector<int> seg_case;
     for (int k = 0; k < n_cases; ++k) {
         const CaseHost& cs = c->cases[k];
         case_segs[k] = make_int2((int)segs.size(), 0);
-        for (int j = 0; j < cs.nf; j += kSegCells) segs.push_back(make_int2(cs.base + j, std::min(kSegCells, cs.nf - j)));
+        for (int j = 0; j < cs.nf; j += kSegCells) {
+            segs.push_back(make_int2(cs.base + j, std::min(kSegCells, cs.nf - j)));
+            seg_case.push_back(k);
+        }
         case_segs[k].y = (int)segs.size() - case_segs[k].x;
         case_rows[k] = make_int2(cs.row_first, cs.nrows);
     }
@@ -648,10 +709,12 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     for (int v = 0; v < kStepVariants; ++v) L.b.blk_case[v] = static_cast<int*>(dev_alloc(c, (size_t)L.nblk[v] * sizeof(int)));
     L.b.segs = static_cast<int2*>(dev_alloc(c, segs.size() * sizeof(int2)));
     L.b.case_segs = static_cast<int2*>(dev_alloc(c, (size_t)n_cases * sizeof(int2)));
+    L.b.seg_case = static_cast<int*>(dev_alloc(c, seg_case.size() * sizeof(int)));
+    L.b.coef = static_cast<double*>(dev_alloc(c, (size_t)n_cases * sizeof(double)));
     L.b.partials = static_cast<double*>(dev_alloc(c, segs.size() * 10 * sizeof(double)));
     L.b.case_out = static_cast<double*>(dev_alloc(c, (size_t)n_cases * kCaseOutSlots * sizeof(double)));
     bool ok = L.b.f[0] && L.b.f[1] && L.b.X[0] && L.b.X[1] && L.b.snap && L.b.nbr && L.b.rows && L.b.case_rows &&
-              L.b.cases && L.b.segs && L.b.case_segs && L.b.partials && L.b.case_out;
+              L.b.cases && L.b.segs && L.b.case_segs && L.b.seg_case && L.b.coef && L.b.partials && L.b.case_out;
     for (int v = 0; v < kStepVariants; ++v) ok = ok && L.b.blk_case[v];
     if (!ok) return bail(fail(c, LBMS_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes + 2 * xbytes + sbytes));
 
@@ -677,6 +740,7 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     up(L.b.case_rows, case_rows.data(), case_rows.size() * sizeof(int2));
     up(L.b.segs, segs.data(), segs.size() * sizeof(int2));
     up(L.b.case_segs, case_segs.data(), case_segs.size() * sizeof(int2));
+    up(L.b.seg_case, seg_case.data(), seg_case.size() * sizeof(int));
     for (int v = 0; v < kStepVariants; ++v) up(L.b.blk_case[v], blk_case[v].data(), blk_case[v].size() * sizeof(int));
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.f[k], 0, fbytes, c->stream);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMemsetAsync(L.b.X[k], 0, xbytes, c->stream);
@@ -764,14 +828,26 @@ lbms_status lbms_batch_run_to_residual(lbms_ctx* c, double tol, int64_t max_step
     int64_t done = 0;
     CK(launch_case_residuals(c->L, 1, c->stream), "residual kernels");  // snapshots start here
     lbms_status st = LBMS_OK;
+    const int64_t W = c->opt.extrapolate_every;
+    Extrapolator ex;
+    if (W > 0) st = extrap_begin(c, ex);
     bool all = false;
-    while (done < max_steps && !all) {
+    while (st == LBMS_OK && done < max_steps && !all) {
         const int64_t k = std::min<int64_t>(K, max_steps - done);
         st = launch_steps(c, k);
         if (st != LBMS_OK) break;
         done += k;
         st = case_residuals(c, (int)k, r.data());
         if (st != LBMS_OK) break;
+        if (W > 0 && (ex.since += k) >= W) {
+            st = extrap_check(c, ex);
+            if (st != LBMS_OK) break;
+            // a jump is never the last thing before a convergence decision:
+            // the next residual check sees it in its K-step change
+            bool any = false;
+            for (double cf : ex.coef) any = any || cf != 0.0;
+            if (any) continue;
+        }
         all = true;
         for (int q = 0; q < n; ++q) {
             if (met[q] < 0 && r[q] <= tol) met[q] = done;

@@ -27,7 +27,10 @@ struct DevBuffers {
     int* blk_case[kStepVariants] = {nullptr, nullptr, nullptr};  // step-kernel block -> case
     int2* segs = nullptr;              // [segments]: first cell, cell count (reduction segments)
     int2* case_segs = nullptr;         // [cases]: first segment, segment count
+    int* seg_case = nullptr;           // [segments]: case of each segment
     double* partials = nullptr;        // [segments][10]
+    double* extrap = nullptr;          // [3][S] X of the last extrapolation check (lazy)
+    double* coef = nullptr;            // [cases] extrapolation factors
     double* case_out = nullptr;        // [cases][10] residual sums, then [cases][6] boundary sums
     void* fields = nullptr;            // [3 + 3 dim][S] of tau and u (lazy), FP64 or FP32
 };
@@ -72,5 +75,8 @@ cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st);
 cudaError_t launch_fields(const Launch& L, cudaStream_t st);
 cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st);
 cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st);
+// per-case sums of (X - E)^2 etc. into case_out[c * 10 + v], E unchanged
+cudaError_t launch_case_extrap_norms(const Launch& L, cudaStream_t st);
+cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st);
 
 }  // namespace lbms

@@ -125,6 +125,20 @@ struct Xv<float> {
     }
 };
 
+// Stores an FP64 value into the X format (double, or hi/lo FP32 words).
+template <typename XS>
+__device__ __forceinline__ void store_x(XS* xb, int64_t S, int s, int i, double v);
+template <>
+__device__ __forceinline__ void store_x<double>(double* xb, int64_t S, int s, int i, double v) {
+    xb[s * S + i] = v;
+}
+template <>
+__device__ __forceinline__ void store_x<float>(float* xb, int64_t S, int s, int i, double v) {
+    const float hi = (float)v;
+    xb[s * S + i] = hi;
+    xb[(3 + s) * S + i] = (float)(v - (double)hi);
+}
+
 // Per-case data of a batch.  Every case owns the fluid-index range
 // [base, base + nf), with base a multiple of kCaseAlign, so that no block of
 // the step kernel spans two cases.
@@ -626,6 +640,33 @@ __global__ void __launch_bounds__(kSegThreads) case_boundary_kernel(
         }
     }
     block_sum<6>(acc, out + (int64_t)blockIdx.x * 6);
+}
+
+// Extrapolation of the slowest decay mode for segment blockIdx.x of case
+// seg_case[blockIdx.x]: with d = X - E (E = X of W steps ago) and
+// c = coef[case], X += c d in both X copies (the step's and the lagged one);
+// E takes the new X.  FP64 arithmetic, run once every W steps.
+template <typename XS>
+__global__ void __launch_bounds__(kSegThreads) seg_extrapolate_kernel(XS* __restrict__ X, XS* __restrict__ Xprev,
+                                                                      double* __restrict__ E, int64_t S,
+                                                                      const int2* __restrict__ segs,
+                                                                      const int* __restrict__ seg_case,
+                                                                      const double* __restrict__ coef) {
+    const int2 sg = segs[blockIdx.x];
+    const double c = coef[seg_case[blockIdx.x]];
+    for (int j = threadIdx.x; j < sg.y; j += kSegThreads) {
+        const int i = sg.x + j;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const double x = Xv<XS>::own(X, S, s, i).to_double();
+            const double xp = Xv<XS>::own(Xprev, S, s, i).to_double();
+            const double d = c * (x - E[s * S + i]);
+            const double xn = x + d;
+            store_x<XS>(X, S, s, i, xn);
+            store_x<XS>(Xprev, S, s, i, xp + d);
+            E[s * S + i] = xn;
+        }
+    }
 }
 
 }  // namespace lbms

@@ -117,6 +117,24 @@ cudaError_t residual_t(const Launch& L, int update, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <typename XS>
+cudaError_t extrap_norms_t(const Launch& L, cudaStream_t st) {
+    seg_residual_kernel<XS><<<L.n_segs, kSegThreads, 0, st>>>(static_cast<const XS*>(L.b.X[L.cur]), L.b.extrap, L.S,
+                                                              L.b.segs, 0, L.b.partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_finalize_kernel<10><<<L.n_cases, kSegThreads, 0, st>>>(L.b.partials, L.b.case_segs, L.b.case_out);
+    return cudaGetLastError();
+}
+
+template <typename XS>
+cudaError_t extrapolate_t(const Launch& L, cudaStream_t st) {
+    seg_extrapolate_kernel<XS><<<L.n_segs, kSegThreads, 0, st>>>(static_cast<XS*>(L.b.X[L.cur]),
+                                                                 static_cast<XS*>(L.b.X[L.cur ^ 1]), L.b.extrap, L.S,
+                                                                 L.b.segs, L.b.seg_case, L.b.coef);
+    return cudaGetLastError();
+}
+
 template <class Lat, typename XS, typename P>
 cudaError_t boundary_t(const Launch& L, cudaStream_t st) {
     // per-case sums land in case_out[n_cases * 10 + c * 6 + v]
@@ -162,6 +180,14 @@ cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st) 
 }
 cudaError_t launch_fields(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(fields_t, L, st); }
 cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st) { LBMS_DISPATCH(boundary_t, L, st); }
+
+cudaError_t launch_case_extrap_norms(const Launch& L, cudaStream_t st) {
+    return L.precision == 0 ? extrap_norms_t<double>(L, st) : extrap_norms_t<float>(L, st);
+}
+
+cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st) {
+    return L.precision == 0 ? extrapolate_t<double>(L, st) : extrapolate_t<float>(L, st);
+}
 
 cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st) {
     return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float>(L, update, st);

@@ -348,3 +348,22 @@ def test_depletion_is_reported(lbms):
     with pytest.raises(lbms.LbmsError) as e:
         s.overpotential()
     assert e.value.status == lbms.LBMS_EDEPLETED
+
+
+def test_extrapolation_keeps_the_steady_state_and_saves_steps(lbms):
+    """Aitken extrapolation of the slowest mode (extrapolate_every) reaches
+    the same steady state in fewer steps."""
+    case = cases.anode_2d_96x48()
+    runs = {}
+    for W in (0, 2000):
+        s = lbms.Solver.from_case(case, precision="fp64", extrapolate_every=W)
+        s.set_bc(case.x_in, case.current_A_cm2)
+        n, r, st = s.run_to_residual(1e-11, 2_000_000)
+        assert st == lbms.LBMS_OK and r <= 1e-11
+        runs[W] = (n, s.fields(), s.overpotential()[0])
+        s.close()
+    (n0, X0, eta0), (n1, X1, eta1) = runs[0], runs[2000]
+    f = ~case.solid
+    assert n1 < 0.8 * n0
+    assert np.abs(X0 - X1)[:, f].max() < 1e-6
+    assert eta1 == pytest.approx(eta0, rel=1e-5)
