@@ -341,7 +341,8 @@ def main():
                            "x_in": list(case.x_in), "precision": args.precision,
                            "parallelism": f"replicas x{ws}",
                            "tile": f"{tinfo.tile_cells} cells x 3 species per block, "
-                                   f"{tinfo.tile_min_blocks} blocks/SM (autotuned)",
+                                   f"{tinfo.tile_min_blocks} blocks/SM, {tinfo.neighbour_bits}-bit "
+                                   f"neighbour table (autotuned)",
                            "l2": "state larger than L2 (no flush needed)" if nf * bpc > 129e6 * 2
                            else "state fits in L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,

@@ -95,6 +95,9 @@ typedef struct {
  *             two successive ratios agree within 2 % and 0.05 < rho < 0.98).
  *             The fixed point is unchanged; only the approach is shortened.
  *             0 = off [0]
+ *  step_variant  0: the autotuner picks the step kernel's tile and neighbour
+ *             table by timing; k > 0 forces variant k - 1 (for tests), an
+ *             unavailable one (16-bit table not built) is an error [0]
  *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
  *  alloc/free device allocator callbacks (e.g. a framework's caching
  *             allocator); NULL = cudaMalloc/cudaFree [NULL] */
@@ -105,6 +108,7 @@ typedef struct {
     double dt_s;
     int check_every;
     int extrapolate_every;
+    int step_variant;
     void *stream;
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);
@@ -128,6 +132,7 @@ typedef struct {
     int n_cases;                /* cases in the handle (1 unless made by lbms_create_batch) */
     int tile_cells;             /* step-kernel tile picked by the autotuner: cells per block */
     int tile_min_blocks;        /*   and its register budget (resident blocks per SM) */
+    int neighbour_bits;         /*   and its neighbour table: 32-bit indices or 16-bit offsets */
 } lbms_info;
 /* n_cells and n_fluid sum over all cases; dx_m, dt_s, q_lat, x_in and
  * current_A_cm2 describe case 0. */

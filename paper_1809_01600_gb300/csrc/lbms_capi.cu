@@ -268,6 +268,14 @@ size_t x_word(int precision) { return precision == LBMS_FP64 ? sizeof(double) : 
 // swapping, so the state is unchanged; the X copy of cur ^ 1 is restored.
 lbms_status autotune(lbms_ctx* c) {
     Launch& L = c->L;
+    if (c->opt.step_variant > 0) {
+        const int v = c->opt.step_variant - 1;
+        if (kVariantNb16[v] && !L.b.nbr16)
+            return fail(c, LBMS_EINVAL, "step variant %d needs the 16-bit neighbour table, which was not built", v);
+        L.variant = v;
+        c->tuned = true;
+        return LBMS_OK;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0), "autotune event");
     CK(cudaEventCreate(&e1), "autotune event");
@@ -275,6 +283,7 @@ lbms_status autotune(lbms_ctx* c) {
     int pick = 0;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < kStepVariants && e == cudaSuccess; ++v) {
+        if (kVariantNb16[v] && !L.b.nbr16) continue;
         e = launch_step_variant(L, v, c->stream);  // warm-up
         if (e != cudaSuccess) break;
         e = cudaEventRecord(e0, c->stream);
@@ -560,6 +569,7 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         lbms_default_options(&c->opt);
     if (c->opt.check_every <= 0) c->opt.check_every = 100;
     if (c->opt.extrapolate_every < 0) c->opt.extrapolate_every = 0;
+    if (c->opt.step_variant < 0 || c->opt.step_variant > kStepVariants) return bail(fail(c, LBMS_EINVAL, "step_variant out of range"));
     if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
     if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
@@ -725,6 +735,37 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         else
             build_neighbours<D3Q19>(c->cases[k], index_of[k], nbr);
     }
+    // the 16-bit offset table; links whose offset does not fit (periodic
+    // wraps) are marked NB16_FAR and read the 32-bit table.  Built when such
+    // links are rare (at most 1 in 16).
+    const int nbw16 = dim == 2 ? nb16_width<D2Q9>() : nb16_width<D3Q19>();
+    std::vector<int16_t> nbr16;
+    {
+        int64_t far = 0, links = 0;
+        for (int64_t i = 0; i < L.ncells; ++i)
+            for (int k = 0; k < c->Q - 1; ++k) {
+                const int v = nbr[(size_t)i * nbw + k];
+                if (v >= 0) {
+                    ++links;
+                    if (v - i < NB16_MIN_OFFSET || v - i > NB16_MAX_OFFSET) ++far;
+                }
+            }
+        if (far * 16 <= links) {
+            nbr16.assign((size_t)nbw16 * L.S, (int16_t)NB16_SOLID);
+            for (int64_t i = 0; i < L.ncells; ++i)
+                for (int k = 0; k < c->Q - 1; ++k) {
+                    const int v = nbr[(size_t)i * nbw + k];
+                    int code;
+                    if (v >= 0)
+                        code = (v - i < NB16_MIN_OFFSET || v - i > NB16_MAX_OFFSET) ? NB16_FAR : (int)(v - i);
+                    else
+                        code = v == NB_SOLID ? NB16_SOLID : (v == NB_INLET ? NB16_INLET : NB16_OUTLET);
+                    nbr16[(size_t)i * nbw16 + k] = (int16_t)code;
+                }
+            L.b.nbr16 = static_cast<int16_t*>(dev_alloc(c, nbr16.size() * sizeof(int16_t)));
+            if (!L.b.nbr16) return bail(fail(c, LBMS_ENOMEM, "device allocation of the 16-bit neighbour table failed"));
+        }
+    }
     std::vector<int> rows;
     rows.reserve(3 * rows_x0.size());
     rows.insert(rows.end(), rows_x0.begin(), rows_x0.end());
@@ -736,6 +777,7 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         c->h2d += n;
     };
     up(L.b.nbr, nbr.data(), nbr.size() * sizeof(int));
+    if (L.b.nbr16) up(L.b.nbr16, nbr16.data(), nbr16.size() * sizeof(int16_t));
     up(L.b.rows, rows.data(), rows.size() * sizeof(int));
     up(L.b.case_rows, case_rows.data(), case_rows.size() * sizeof(int2));
     up(L.b.segs, segs.data(), segs.size() * sizeof(int2));
@@ -1009,6 +1051,7 @@ lbms_status lbms_get_info(const lbms_ctx* c, lbms_info* info) {
     info->n_cases = (int)c->cases.size();
     info->tile_cells = kVariantCells[c->L.variant];
     info->tile_min_blocks = kVariantMinBlocks[c->L.variant];
+    info->neighbour_bits = kVariantNb16[c->L.variant] ? 16 : 32;
     return LBMS_OK;
 }
 

@@ -10,21 +10,24 @@ namespace lbms {
 
 constexpr int kCaseOutSlots = 16;      // doubles per case: residual sums (10) | boundary sums (6)
 
-// Tile shapes of the step kernel the autotuner chooses from:
-// (cells per block, minimum resident blocks per SM for the register budget).
-constexpr int kStepVariants = 3;
-constexpr int kVariantCells[kStepVariants] = {32, 32, 64};
-constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4};
+// Step-kernel variants the autotuner chooses from: (cells per block, minimum
+// resident blocks per SM for the register budget, neighbour table of 16-bit
+// offsets instead of 32-bit indices).
+constexpr int kStepVariants = 6;
+constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64};
+constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4};
+constexpr int kVariantNb16[kStepVariants] = {0, 0, 0, 1, 1, 1};
 
 struct DevBuffers {
     void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]
     void* X[2] = {nullptr, nullptr};   // mole fractions (double or double-float blocks)
     double* snap = nullptr;            // residual snapshot, [3][S]
     int* nbr = nullptr;                // [S][nb_width]
+    int16_t* nbr16 = nullptr;          // [S][nb16_width] offsets, when they all fit (else null)
     int* rows = nullptr;               // [3][total rows]: x = 0, x = 1, x = nx-1 cell of each row (-1 if solid)
     int2* case_rows = nullptr;         // [cases]: first row, row count
     void* cases = nullptr;             // [cases] CaseBC<XS> (inlet values, outlet flux, range)
-    int* blk_case[kStepVariants] = {nullptr, nullptr, nullptr};  // step-kernel block -> case
+    int* blk_case[kStepVariants] = {};  // step-kernel block -> case
     int2* segs = nullptr;              // [segments]: first cell, cell count (reduction segments)
     int2* case_segs = nullptr;         // [cases]: first segment, segment count
     int* seg_case = nullptr;           // [segments]: case of each segment
@@ -43,7 +46,7 @@ struct Launch {
     int n_cases = 1;
     int total_rows = 0;
     int n_segs = 0;
-    int nblk[kStepVariants] = {0, 0, 0};
+    int nblk[kStepVariants] = {};
     int variant = 0;                   // chosen step-kernel tile shape
     int cur = 0;                       // lattice holding the latest post-collision state
     DevBuffers b;

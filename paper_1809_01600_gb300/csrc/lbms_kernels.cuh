@@ -13,6 +13,8 @@
 //               h = f* - w_k X, in FP64, FP32 or FP16 (FP16 scaled by 2^14).
 //   nbr[i][k-1] fluid index of the source cell x - e_k, or an NB_* code;
 //               one row of nb_width() ints per cell, read with 16-byte loads.
+//               Where every offset fits, a second table holds src - i in 16
+//               bits (nb16_width() per row) and the autotuner may pick it.
 // A pulled population is f_k(x) = w_k X(src) + h_k(src).  The step works on
 // d_k = f_k(x) - w_k X_old(x) ~ w_k (X(src) - X_old(x)) + h_k(src): small
 // numbers whose exchange terms w_k (X(src) - X(x)) are exactly antisymmetric
@@ -62,6 +64,35 @@ __device__ __forceinline__ void load_neighbours(const int* __restrict__ nbr, int
     }
 }
 
+// Output stores of the step kernel.
+template <typename V>
+__device__ __forceinline__ void step_store(V* ptr, V v) {
+    *ptr = v;
+}
+
+// The same row from the 16-bit offset table (links marked NB16_FAR read the
+// 32-bit table).
+template <class L>
+__device__ __forceinline__ void load_neighbours(const int16_t* __restrict__ nbr, const int* __restrict__ nbr32,
+                                                int i, int (&nb)[L::Q]) {
+    constexpr int NW = nb16_width<L>();
+    const int4* row = reinterpret_cast<const int4*>(nbr + (int64_t)i * NW);
+#pragma unroll
+    for (int j = 0; j < NW / 8; ++j) {
+        const int4 v = __ldg(row + j);
+        const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+            const int k = 1 + 8 * j + h;
+            if (k < L::Q) {
+                const int d = (h & 1) ? (w[h >> 1] >> 16) : ((w[h >> 1] << 16) >> 16);
+                nb[k] = d < NB16_MIN_OFFSET ? (NB16_SOLID - 1 - d) : i + d;
+                if (d == NB16_FAR) nb[k] = __ldg(nbr32 + (int64_t)i * nb_width<L>() + (k - 1));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------ storage
 // Non-equilibrium populations: P = T, or __half holding h * 2^14.
 constexpr float kHalfScale = 16384.0f;
@@ -97,6 +128,9 @@ struct Xv<double> {
     __device__ __forceinline__ double to_double() const { return v; }
     __device__ __forceinline__ Xv plus(T d) const { return Xv{v + d}; }
     __device__ __forceinline__ void store(double* xb, int64_t S, int s, int i) const { xb[s * S + i] = v; }
+    __device__ __forceinline__ void store_stream(double* xb, int64_t S, int s, int i) const {
+        step_store(xb + s * S + i, v);
+    }
 };
 template <>
 struct Xv<float> {
@@ -122,6 +156,10 @@ struct Xv<float> {
     __device__ __forceinline__ void store(float* xb, int64_t S, int s, int i) const {
         xb[s * S + i] = hi;
         xb[(3 + s) * S + i] = lo;
+    }
+    __device__ __forceinline__ void store_stream(float* xb, int64_t S, int s, int i) const {
+        step_store(xb + s * S + i, hi);
+        step_store(xb + (3 + s) * S + i, lo);
     }
 };
 
@@ -152,13 +190,14 @@ struct CaseBC {
     int nf;                           // fluid cells of the case
 };
 
-template <typename XS, typename P>
+template <typename XS, typename P, typename NBT>
 struct StepParams {
     const P* __restrict__ hin;
     P* __restrict__ hout;
     const XS* __restrict__ xin;
     XS* __restrict__ xout;
-    const int* __restrict__ nbr;
+    const NBT* __restrict__ nbr;
+    const int* __restrict__ nbr32;      // the 32-bit table (for NB16_FAR links)
     const CaseBC<XS>* __restrict__ cases;
     const int* __restrict__ blk_case;   // case of each block of W cells
     int64_t S;
@@ -242,7 +281,7 @@ __device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], co
             vn2 += v[d] * v[d];
         }
         if (vn2 > T(kVMax * kVMax)) {
-            const T sc = T(kVMax) / sqrt(vn2);
+            const T sc = T(kVMax) * rsqrt(vn2);
 #pragma unroll
             for (int d = 0; d < DIM; ++d) v[d] *= sc;
         }
@@ -262,8 +301,8 @@ __device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], co
 // of a warp walks consecutive cells of one species row.  The three threads of
 // a cell meet once, through shared memory, to exchange X and its gradient for
 // the coupling (which needs all species).
-template <class L, typename XS, typename P, int W, int MB>
-__global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P> p) {
+template <class L, typename XS, typename P, typename NBT, int W, int MB>
+__global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P, NBT> p) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
     constexpr int Q = L::Q;
@@ -288,7 +327,10 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P>
     T dX = T(0);
     {
         nb[0] = i;
-        load_neighbours<L>(p.nbr, i, nb);
+        if constexpr (sizeof(NBT) == 2)
+            load_neighbours<L>(p.nbr, p.nbr32, i, nb);
+        else
+            load_neighbours<L>(p.nbr, i, nb);
         xo = XV::own(p.xin, S, s, i);
         T dxs[Q];    // X(src) - X_old(x) for fluid sources, 0 otherwise
         constexpr T wx = T(weight_xplus<L>());
@@ -306,16 +348,20 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P>
             const T hv = Pop<T, P>::load(hp);
             const T dx = xo.exch(XV::nb(p.xin, S, s, fluid ? src : i));
             T val = T(weight<L>(k)) * dx + hv;
-            if (src == NB_OUTLET) val -= (T(weight<L>(opp<L>(k))) / wx) * qs;
+            // only links entering from x = nx (e_x = -1) can carry the outlet flux
+            if (L::e(k, 0) == -1) val -= (src == NB_OUTLET ? T(weight<L>(opp<L>(k))) / wx : T(0)) * qs;
             d[k] = val;
             dxs[k] = dx;
         }
         // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
         const XV xb = cb.xbc[s];
+        const T din = xb.minus(xo);
 #pragma unroll
         for (int k = 0; k < Q; ++k) {
-            if (L::e(k, 0) == 1 && nb[k] == NB_INLET)
-                d[k] = T(weight<L>(k) + weight<L>(opp<L>(k))) * xb.minus(xo) - d[opp<L>(k)];
+            if (L::e(k, 0) == 1) {
+                const T inl = T(weight<L>(k) + weight<L>(opp<L>(k))) * din - d[opp<L>(k)];
+                d[k] = nb[k] == NB_INLET ? inl : d[k];
+            }
         }
         // lagged gradient (Eq. 35 as central differences) from the differences at hand
 #pragma unroll
@@ -361,11 +407,11 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P>
         const T hk = (d[k] - w * dX) * keep + T(3) * w * Xs * ev * it;
         const P q = Pop<T, P>::quant(hk);
         rest -= Pop<T, P>::dequant(q);
-        ho[k * S32 + i] = q;
+        step_store(ho + k * S32 + i, q);
     }
     // the rest population closes sum_k h_k = 0 (mass) on the stored values
-    ho[i] = Pop<T, P>::quant(rest);
-    xn.store(p.xout, S, s, i);
+    step_store(ho + i, Pop<T, P>::quant(rest));
+    xn.store_stream(p.xout, S, s, i);
 }
 
 // -------------------------------------------------------------------------

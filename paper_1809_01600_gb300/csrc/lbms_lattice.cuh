@@ -70,6 +70,23 @@ __host__ __device__ constexpr int nb_width() {
     return ((L::Q - 1) + 3) / 4 * 4;
 }
 
+// The compact table: 16-bit offsets src - i, rows padded to a multiple of 8
+// entries (16-byte loads); the three lowest values stand for the NB_* codes
+// and the fourth (NB16_FAR) sends the link to the 32-bit table (periodic
+// wraps, whose offsets do not fit).
+template <class L>
+__host__ __device__ constexpr int nb16_width() {
+    return ((L::Q - 1) + 7) / 8 * 8;
+}
+enum : int {
+    NB16_SOLID = -32768,
+    NB16_INLET = -32767,
+    NB16_OUTLET = -32766,
+    NB16_FAR = -32765,
+    NB16_MIN_OFFSET = -32764,   // smallest offset a fluid source may have
+    NB16_MAX_OFFSET = 32767
+};
+
 // Neighbour-table codes for a link whose source x - e_k is not a fluid cell.
 enum : int {
     NB_SOLID = -1,   // half-way bounce-back

@@ -60,29 +60,38 @@ void pack_t(const CaseHostBC& h, void* dst) {
     std::memcpy(dst, &c, sizeof(c));
 }
 
-template <class Lat, typename XS, typename P, int W, int MB>
+template <class Lat, typename XS, typename P, typename NBT, int W, int MB>
 cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
     using T = typename Xv<XS>::T;
-    StepParams<XS, P> p;
+    StepParams<XS, P, NBT> p;
     p.hin = static_cast<const P*>(L.b.f[L.cur]);
     p.hout = static_cast<P*>(L.b.f[L.cur ^ 1]);
     p.xin = static_cast<const XS*>(L.b.X[L.cur]);
     p.xout = static_cast<XS*>(L.b.X[L.cur ^ 1]);
-    p.nbr = L.b.nbr;
+    if constexpr (sizeof(NBT) == 2)
+        p.nbr = L.b.nbr16;
+    else
+        p.nbr = L.b.nbr;
+    p.nbr32 = L.b.nbr;
     p.cases = static_cast<const CaseBC<XS>*>(L.b.cases);
     p.blk_case = L.b.blk_case[variant];
     p.S = L.S;
     p.c = make_const<T>(L);
-    step_kernel<Lat, XS, P, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
+    step_kernel<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
     return cudaGetLastError();
 }
 
 template <class Lat, typename XS, typename P>
 cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
-    static_assert(kStepVariants == 3, "variant table");
-    if (variant == 0) return step_w<Lat, XS, P, kVariantCells[0], kVariantMinBlocks[0]>(L, 0, st);
-    if (variant == 1) return step_w<Lat, XS, P, kVariantCells[1], kVariantMinBlocks[1]>(L, 1, st);
-    return step_w<Lat, XS, P, kVariantCells[2], kVariantMinBlocks[2]>(L, 2, st);
+    static_assert(kStepVariants == 6, "variant table");
+    switch (variant) {
+        case 0: return step_w<Lat, XS, P, int, kVariantCells[0], kVariantMinBlocks[0]>(L, 0, st);
+        case 1: return step_w<Lat, XS, P, int, kVariantCells[1], kVariantMinBlocks[1]>(L, 1, st);
+        case 2: return step_w<Lat, XS, P, int, kVariantCells[2], kVariantMinBlocks[2]>(L, 2, st);
+        case 3: return step_w<Lat, XS, P, int16_t, kVariantCells[3], kVariantMinBlocks[3]>(L, 3, st);
+        case 4: return step_w<Lat, XS, P, int16_t, kVariantCells[4], kVariantMinBlocks[4]>(L, 4, st);
+        default: return step_w<Lat, XS, P, int16_t, kVariantCells[5], kVariantMinBlocks[5]>(L, 5, st);
+    }
 }
 
 template <class Lat, typename XS, typename P>

@@ -62,7 +62,7 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("coupling", C.c_int), ("tau_min", C.c_double),
                 ("tau_max", C.c_double), ("dt_s", C.c_double), ("check_every", C.c_int),
-                ("extrapolate_every", C.c_int),
+                ("extrapolate_every", C.c_int), ("step_variant", C.c_int),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", C.c_void_p)]
 
@@ -75,7 +75,7 @@ class Info(C.Structure):
                 ("current_A_cm2", C.c_double), ("steps", C.c_int64),
                 ("device_bytes", C.c_size_t), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_cases", C.c_int), ("tile_cells", C.c_int),
-                ("tile_min_blocks", C.c_int)]
+                ("tile_min_blocks", C.c_int), ("neighbour_bits", C.c_int)]
 
 
 _lib = None
@@ -138,7 +138,7 @@ class _Handle:
 
     def _setup(self, molar_mass, fuller_volume, stoich, electrons, D_binary, pore_diameter,
                eps_over_tau, precision, coupling, tau_min, tau_max, dt, check_every, stream,
-               torch_allocator, extrapolate_every=0):
+               torch_allocator, extrapolate_every=0, step_variant=0):
         lib = load()
         self._lib = lib
         self._mm = np.ascontiguousarray(molar_mass, dtype=np.float64)
@@ -161,6 +161,7 @@ class _Handle:
         o.dt_s = float(dt or 0.0)
         o.check_every = int(check_every)
         o.extrapolate_every = int(extrapolate_every)
+        o.step_variant = int(step_variant)
         self._keep = []
         if stream is None or torch_allocator:
             try:
@@ -253,13 +254,13 @@ class Batch(_Handle):
 
     def __init__(self, solids, dim=None, length_x=2e-3, periodic_x=False, *, T=1073.0, p=101325.0,
                  precision="fp32", coupling="ms", tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100,
-                 stream=None, torch_allocator=True, extrapolate_every=0, **gas):
+                 stream=None, torch_allocator=True, extrapolate_every=0, step_variant=0, **gas):
         g = dict(_GAS_DEFAULTS)
         g.update(gas)
         sp, df, o = self._setup(g["molar_mass"], g["fuller_volume"], g["stoich"], g["electrons"],
                                 g["D_binary"], g["pore_diameter"], g["eps_over_tau"], precision,
                                 coupling, tau_min, tau_max, dt, check_every, stream, torch_allocator,
-                                extrapolate_every)
+                                extrapolate_every, step_variant)
         n = len(solids)
         lx = list(length_x) if np.ndim(length_x) else [length_x] * n
         px = list(periodic_x) if np.ndim(periodic_x) else [periodic_x] * n
@@ -346,10 +347,11 @@ class Solver(_Handle):
                  stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
                  eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
                  tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
-                 torch_allocator=True, extrapolate_every=0):
+                 torch_allocator=True, extrapolate_every=0, step_variant=0):
         sp, df, o = self._setup(molar_mass, fuller_volume, stoich, electrons, D_binary,
                                 pore_diameter, eps_over_tau, precision, coupling, tau_min, tau_max,
-                                dt, check_every, stream, torch_allocator, extrapolate_every)
+                                dt, check_every, stream, torch_allocator, extrapolate_every,
+                                step_variant)
         g, mask, shape, dim = self._geometry(solid, dim, length_x, periodic_x)
         self._mask = mask
         self.shape = shape

@@ -86,3 +86,34 @@ def test_batch_rejects_mixed_dims(L):
     with pytest.raises(L.LbmsError) as e:
         L.Batch([a.solid, c.solid], dim=None)
     assert e.value.status == L.LBMS_EINVAL
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-7)])
+def test_every_step_variant_gives_the_same_fields(L, variant, precision, tol):
+    """All tile shapes and both neighbour-table formats the autotuner may pick
+    compute the same step (to rounding of FMA contraction)."""
+    c = cases.porous((12, 14, 30), radius=2, porosity=0.5, seed=71, current_A_cm2=1.5)
+    ref = L.Solver.from_case(c, precision=precision, step_variant=1)
+    s = L.Solver.from_case(c, precision=precision, step_variant=variant)
+    for h in (ref, s):
+        h.set_bc(c.x_in, c.current_A_cm2)
+        h.step(77)
+    i = s.info()
+    assert i.neighbour_bits == (16 if variant >= 4 else 32)
+    assert np.abs(s.fields() - ref.fields()).max() <= tol
+
+
+@pytest.mark.parametrize("variant", [1, 4])
+def test_far_links_of_the_16_bit_table(L, variant):
+    """A box long in z: the periodic wrap in z gives offsets beyond 16 bits,
+    which the 16-bit table sends to the 32-bit table."""
+    c = cases.porous((96, 40, 24), radius=2, porosity=0.5, seed=72, current_A_cm2=1.0)
+    o = Oracle(c)
+    s = L.Solver.from_case(c, precision="fp64", step_variant=variant)
+    s.set_bc(c.x_in, c.current_A_cm2)
+    s.step(40)
+    o.step(40)
+    assert s.info().neighbour_bits == (16 if variant >= 4 else 32)
+    f = ~c.solid
+    assert np.abs(s.fields() - o.X)[:, f].max() <= 1e-11
