@@ -95,9 +95,11 @@ typedef struct {
  *             two successive ratios agree within 2 % and 0.05 < rho < 0.98).
  *             The fixed point is unchanged; only the approach is shortened.
  *             0 = off [0]
- *  step_variant  0: the autotuner picks the step kernel's tile and neighbour
- *             table by timing; k > 0 forces variant k - 1 (for tests), an
- *             unavailable one (16-bit table not built) is an error [0]
+ *  step_variant  0: the autotuner picks the step kernel's tile, thread
+ *             mapping (a thread per cell and species, or per cell) and
+ *             neighbour table by timing; k in 1..8 forces variant k - 1 (for
+ *             tests), an unavailable one (16-bit table not built) is an
+ *             error [0]
  *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
  *  alloc/free device allocator callbacks (e.g. a framework's caching
  *             allocator); NULL = cudaMalloc/cudaFree [NULL] */

@@ -12,11 +12,13 @@ constexpr int kCaseOutSlots = 16;      // doubles per case: residual sums (10) |
 
 // Step-kernel variants the autotuner chooses from: (cells per block, minimum
 // resident blocks per SM for the register budget, neighbour table of 16-bit
-// offsets instead of 32-bit indices).
-constexpr int kStepVariants = 6;
-constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64};
-constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4};
-constexpr int kVariantNb16[kStepVariants] = {0, 0, 0, 1, 1, 1};
+// offsets instead of 32-bit indices, one thread per cell for all species
+// instead of one per (cell, species)).
+constexpr int kStepVariants = 8;
+constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64, 64, 64};
+constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4, 8, 6};
+constexpr int kVariantNb16[kStepVariants] = {0, 0, 0, 1, 1, 1, 0, 0};
+constexpr int kVariantPerCell[kStepVariants] = {0, 0, 0, 0, 0, 0, 1, 1};
 
 struct DevBuffers {
     void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]

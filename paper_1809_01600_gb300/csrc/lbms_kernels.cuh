@@ -120,6 +120,9 @@ struct Xv<double> {
     using T = double;
     double v;
     __device__ __forceinline__ static Xv own(const double* xb, int64_t S, int s, int i) { return Xv{xb[s * S + i]}; }
+    // with the species rows already located (hi = the FP64 row; lo unused)
+    __device__ __forceinline__ static Xv own_rows(const double* hi, const double*, int i) { return Xv{hi[i]}; }
+    __device__ __forceinline__ void store_rows(double* hi, double*, int i) const { step_store(hi + i, v); }
     // value of a neighbour as used by the exchange terms and the gradient
     __device__ __forceinline__ static T nb(const double* xb, int64_t S, int s, int j) { return xb[s * S + j]; }
     __device__ __forceinline__ T exch(T n) const { return n - v; }          // neighbour minus own
@@ -128,9 +131,6 @@ struct Xv<double> {
     __device__ __forceinline__ double to_double() const { return v; }
     __device__ __forceinline__ Xv plus(T d) const { return Xv{v + d}; }
     __device__ __forceinline__ void store(double* xb, int64_t S, int s, int i) const { xb[s * S + i] = v; }
-    __device__ __forceinline__ void store_stream(double* xb, int64_t S, int s, int i) const {
-        step_store(xb + s * S + i, v);
-    }
 };
 template <>
 struct Xv<float> {
@@ -138,6 +138,11 @@ struct Xv<float> {
     float hi, lo;
     __device__ __forceinline__ static Xv own(const float* xb, int64_t S, int s, int i) {
         return Xv{xb[s * S + i], xb[(3 + s) * S + i]};
+    }
+    __device__ __forceinline__ static Xv own_rows(const float* hi, const float* lo, int i) { return Xv{hi[i], lo[i]}; }
+    __device__ __forceinline__ void store_rows(float* h, float* l, int i) const {
+        step_store(h + i, hi);
+        step_store(l + i, lo);
     }
     __device__ __forceinline__ static T nb(const float* xb, int64_t S, int s, int j) { return xb[s * S + j]; }
     // hi_n - hi is exact for neighbouring values and antisymmetric between two cells
@@ -156,10 +161,6 @@ struct Xv<float> {
     __device__ __forceinline__ void store(float* xb, int64_t S, int s, int i) const {
         xb[s * S + i] = hi;
         xb[(3 + s) * S + i] = lo;
-    }
-    __device__ __forceinline__ void store_stream(float* xb, int64_t S, int s, int i) const {
-        step_store(xb + s * S + i, hi);
-        step_store(xb + (3 + s) * S + i, lo);
     }
 };
 
@@ -320,6 +321,8 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
     const int64_t S = p.S;
     const int S32 = (int)S;      // Q * S < 2^31 (checked at create): 32-bit offsets in a species block
     const P* hs = p.hin + (int64_t)s * Q * S;
+    const XS* xhi = p.xin + (int64_t)s * S;         // X rows of this species (hi, lo)
+    const XS* xlo = p.xin + (int64_t)(3 + s) * S;   // (lo row only read in the pair format)
 
     int nb[Q];
     T d[Q];          // f_k(x) - w_k X_old(x) after streaming
@@ -331,7 +334,7 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
             load_neighbours<L>(p.nbr, p.nbr32, i, nb);
         else
             load_neighbours<L>(p.nbr, i, nb);
-        xo = XV::own(p.xin, S, s, i);
+        xo = XV::own_rows(xhi, xlo, i);
         T dxs[Q];    // X(src) - X_old(x) for fluid sources, 0 otherwise
         constexpr T wx = T(weight_xplus<L>());
         const T qs = cb.qout[s];
@@ -346,7 +349,7 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
             const bool fluid = src >= 0;
             const P* hp = hs + (fluid ? k * S32 + src : opp<L>(k) * S32 + i);
             const T hv = Pop<T, P>::load(hp);
-            const T dx = xo.exch(XV::nb(p.xin, S, s, fluid ? src : i));
+            const T dx = xo.exch(xhi[fluid ? src : i]);
             T val = T(weight<L>(k)) * dx + hv;
             // only links entering from x = nx (e_x = -1) can carry the outlet flux
             if (L::e(k, 0) == -1) val -= (src == NB_OUTLET ? T(weight<L>(opp<L>(k))) / wx : T(0)) * qs;
@@ -411,7 +414,112 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
     }
     // the rest population closes sum_k h_k = 0 (mass) on the stored values
     step_store(ho + i, Pop<T, P>::quant(rest));
-    xn.store_stream(p.xout, S, s, i);
+    xn.store_rows(p.xout + (int64_t)s * S, p.xout + (int64_t)(3 + s) * S, i);
+}
+
+// -------------------------------------------------------------------------
+// The same time step with one thread per fluid cell handling all three
+// species: the neighbour decode, the address selection of every link and
+// the part of the coupling common to the species are done once per cell
+// instead of once per species thread, at the price of more registers.
+template <class L, typename XS, typename P, typename NBT, int W, int MB>
+__global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P, NBT> p) {
+    using T = typename Xv<XS>::T;
+    using XV = Xv<XS>;
+    constexpr int Q = L::Q;
+    constexpr int DIM = L::DIM;
+    const int i = blockIdx.x * W + threadIdx.x;
+    const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
+    const int64_t S = p.S;
+    const int S32 = (int)S;
+
+    int nb[Q];
+    nb[0] = i;
+    if constexpr (sizeof(NBT) == 2)
+        load_neighbours<L>(p.nbr, p.nbr32, i, nb);
+    else
+        load_neighbours<L>(p.nbr, i, nb);
+
+    XV xo[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) xo[s] = XV::own_rows(p.xin + (int64_t)s * S, p.xin + (int64_t)(3 + s) * S, i);
+
+    constexpr T wx = T(weight_xplus<L>());
+    T d[3][Q];
+    T dxa[3][2 * DIM + 1];   // X(src) - X_old(x) on the axis links (gradient)
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        d[s][0] = Pop<T, P>::load(p.hin + (int64_t)s * Q * S + i);
+        dxa[s][0] = T(0);
+    }
+#pragma unroll
+    for (int k = 1; k < Q; ++k) {
+        const int src = nb[k];
+        const bool fluid = src >= 0;
+        const int hoff = fluid ? k * S32 + src : opp<L>(k) * S32 + i;
+        const int xidx = fluid ? src : i;
+        const T oc = (L::e(k, 0) == -1 && src == NB_OUTLET) ? T(weight<L>(opp<L>(k))) / wx : T(0);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const T hv = Pop<T, P>::load(p.hin + (int64_t)s * Q * S + hoff);
+            const T dx = xo[s].exch(p.xin[(int64_t)s * S + xidx]);
+            T val = T(weight<L>(k)) * dx + hv;
+            if (L::e(k, 0) == -1) val -= oc * cb.qout[s];
+            d[s][k] = val;
+            if (k <= 2 * DIM) dxa[s][k] = dx;
+        }
+    }
+    T X[3], dX[3], g[3][DIM];
+    XV xn[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
+        const T din = cb.xbc[s].minus(xo[s]);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) {
+            if (L::e(k, 0) == 1) {
+                const T inl = T(weight<L>(k) + weight<L>(opp<L>(k))) * din - d[s][opp<L>(k)];
+                d[s][k] = nb[k] == NB_INLET ? inl : d[s][k];
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            const int kp = 2 + 2 * a, km = 1 + 2 * a;
+            const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
+            const T pv = dxa[s][kp], mv = dxa[s][km];
+            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+        }
+        T acc = T(0);
+#pragma unroll
+        for (int k = 0; k < Q; ++k) acc += d[s][k];
+        dX[s] = acc;
+        xn[s] = xo[s].plus(acc);
+        X[s] = xn[s].value();
+    }
+
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        T J[DIM], vs[DIM], ts, xinv;
+        ms_flux<T, DIM>(X, g, p.c, s, J);
+        ms_relax<T, DIM>(X, g[s], J, p.c, s, ts, vs, xinv);
+        const T it = Arith<T>::div(T(1), ts);
+        const T keep = T(1) - it;
+        P* ho = p.hout + (int64_t)s * Q * S;
+        T rest = T(0);
+#pragma unroll
+        for (int k = 1; k < Q; ++k) {
+            T ev = T(0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) ev += T(L::e(k, a)) * vs[a];
+            const T w = T(weight<L>(k));
+            const T hk = (d[s][k] - w * dX[s]) * keep + T(3) * w * X[s] * ev * it;
+            const P q = Pop<T, P>::quant(hk);
+            rest -= Pop<T, P>::dequant(q);
+            step_store(ho + k * S32 + i, q);
+        }
+        step_store(ho + i, Pop<T, P>::quant(rest));
+        xn[s].store_rows(p.xout + (int64_t)s * S, p.xout + (int64_t)(3 + s) * S, i);
+    }
 }
 
 // -------------------------------------------------------------------------

@@ -60,7 +60,7 @@ void pack_t(const CaseHostBC& h, void* dst) {
     std::memcpy(dst, &c, sizeof(c));
 }
 
-template <class Lat, typename XS, typename P, typename NBT, int W, int MB>
+template <class Lat, typename XS, typename P, typename NBT, int W, int MB, bool PER_CELL = false>
 cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
     using T = typename Xv<XS>::T;
     StepParams<XS, P, NBT> p;
@@ -77,20 +77,26 @@ cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
     p.blk_case = L.b.blk_case[variant];
     p.S = L.S;
     p.c = make_const<T>(L);
-    step_kernel<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
+    if constexpr (PER_CELL)
+        step_kernel_cell<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], W, 0, st>>>(p);
+    else
+        step_kernel<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
     return cudaGetLastError();
 }
 
 template <class Lat, typename XS, typename P>
 cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
-    static_assert(kStepVariants == 6, "variant table");
+    static_assert(kStepVariants == 8 && kVariantPerCell[6] && kVariantPerCell[7] && !kVariantPerCell[5],
+                  "variant table");
     switch (variant) {
         case 0: return step_w<Lat, XS, P, int, kVariantCells[0], kVariantMinBlocks[0]>(L, 0, st);
         case 1: return step_w<Lat, XS, P, int, kVariantCells[1], kVariantMinBlocks[1]>(L, 1, st);
         case 2: return step_w<Lat, XS, P, int, kVariantCells[2], kVariantMinBlocks[2]>(L, 2, st);
         case 3: return step_w<Lat, XS, P, int16_t, kVariantCells[3], kVariantMinBlocks[3]>(L, 3, st);
         case 4: return step_w<Lat, XS, P, int16_t, kVariantCells[4], kVariantMinBlocks[4]>(L, 4, st);
-        default: return step_w<Lat, XS, P, int16_t, kVariantCells[5], kVariantMinBlocks[5]>(L, 5, st);
+        case 5: return step_w<Lat, XS, P, int16_t, kVariantCells[5], kVariantMinBlocks[5]>(L, 5, st);
+        case 6: return step_w<Lat, XS, P, int, kVariantCells[6], kVariantMinBlocks[6], true>(L, 6, st);
+        default: return step_w<Lat, XS, P, int, kVariantCells[7], kVariantMinBlocks[7], true>(L, 7, st);
     }
 }
 
