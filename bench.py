@@ -340,7 +340,8 @@ def main():
                            "porosity": round(case.porosity, 4), "current_A_cm2": case.current_A_cm2,
                            "x_in": list(case.x_in), "precision": args.precision,
                            "parallelism": f"replicas x{ws}",
-                           "tile": f"{tinfo.tile_cells} cells x 3 species per block, "
+                           "tile": f"{tinfo.tile_cells} cells per block, "
+                                   f"{'one thread per cell' if tinfo.threads_per_cell == 1 else 'one thread per cell and species'}, "
                                    f"{tinfo.tile_min_blocks} blocks/SM, {tinfo.neighbour_bits}-bit "
                                    f"neighbour table (autotuned)",
                            "l2": "state larger than L2 (no flush needed)" if nf * bpc > 129e6 * 2

@@ -135,6 +135,7 @@ typedef struct {
     int tile_cells;             /* step-kernel tile picked by the autotuner: cells per block */
     int tile_min_blocks;        /*   and its register budget (resident blocks per SM) */
     int neighbour_bits;         /*   and its neighbour table: 32-bit indices or 16-bit offsets */
+    int threads_per_cell;       /*   and its thread mapping: 3 (one per species) or 1 */
 } lbms_info;
 /* n_cells and n_fluid sum over all cases; dx_m, dt_s, q_lat, x_in and
  * current_A_cm2 describe case 0. */

@@ -1052,6 +1052,7 @@ lbms_status lbms_get_info(const lbms_ctx* c, lbms_info* info) {
     info->tile_cells = kVariantCells[c->L.variant];
     info->tile_min_blocks = kVariantMinBlocks[c->L.variant];
     info->neighbour_bits = kVariantNb16[c->L.variant] ? 16 : 32;
+    info->threads_per_cell = kVariantPerCell[c->L.variant] ? 1 : 3;
     return LBMS_OK;
 }
 

@@ -15,8 +15,8 @@ constexpr int kCaseOutSlots = 16;      // doubles per case: residual sums (10) |
 // offsets instead of 32-bit indices, one thread per cell for all species
 // instead of one per (cell, species)).
 constexpr int kStepVariants = 8;
-constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64, 64, 64};
-constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4, 8, 6};
+constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64, 64, 32};
+constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4, 8, 16};
 constexpr int kVariantNb16[kStepVariants] = {0, 0, 0, 1, 1, 1, 0, 0};
 constexpr int kVariantPerCell[kStepVariants] = {0, 0, 0, 0, 0, 0, 1, 1};
 

@@ -98,17 +98,27 @@ __device__ __forceinline__ void load_neighbours(const int16_t* __restrict__ nbr,
 constexpr float kHalfScale = 16384.0f;
 constexpr float kHalfInvScale = 1.0f / 16384.0f;
 
+// load / quant / dequant work in lattice units; raw / quant_raw /
+// dequant_raw in storage units (lattice value times kStore).
 template <typename T, typename P>
 struct Pop {
+    static constexpr float kStore = 1.0f;
     __device__ __forceinline__ static T load(const P* p) { return T(*p); }
     __device__ __forceinline__ static P quant(T v) { return P(v); }
     __device__ __forceinline__ static T dequant(P v) { return T(v); }
+    __device__ __forceinline__ static T raw(const P* p) { return T(*p); }
+    __device__ __forceinline__ static P quant_raw(T v) { return P(v); }
+    __device__ __forceinline__ static T dequant_raw(P v) { return T(v); }
 };
 template <>
 struct Pop<float, __half> {
+    static constexpr float kStore = kHalfScale;
     __device__ __forceinline__ static float load(const __half* p) { return __half2float(*p) * kHalfInvScale; }
     __device__ __forceinline__ static __half quant(float v) { return __float2half_rn(v * kHalfScale); }
     __device__ __forceinline__ static float dequant(__half v) { return __half2float(v) * kHalfInvScale; }
+    __device__ __forceinline__ static float raw(const __half* p) { return __half2float(*p); }
+    __device__ __forceinline__ static __half quant_raw(float v) { return __float2half_rn(v); }
+    __device__ __forceinline__ static float dequant_raw(__half v) { return __half2float(v); }
 };
 
 // Mole fractions.  Xv<double>: one FP64 value.  Xv<float>: a double-float
@@ -419,19 +429,33 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
 
 // -------------------------------------------------------------------------
 // The same time step with one thread per fluid cell handling all three
-// species: the neighbour decode, the address selection of every link and
-// the part of the coupling common to the species are done once per cell
-// instead of once per species thread, at the price of more registers.
+// species: the neighbour decode and the address selection of every link are
+// done once per cell instead of once per species thread.  The streamed
+// populations d_k wait for the coupling in shared memory (each thread reads
+// back only its own column, so no barrier), which keeps the register count
+// low enough for a useful number of resident warps.  Everything from the
+// gather to the store runs in storage units (h * kStore), so the FP16
+// scaling costs one multiply per species instead of one per population.
 template <class L, typename XS, typename P, typename NBT, int W, int MB>
 __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P, NBT> p) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
-    const int i = blockIdx.x * W + threadIdx.x;
+    constexpr T sc = T(Pop<T, P>::kStore);
+    __shared__ T sD[3][Q][W];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * W + t;
     const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
     const int64_t S = p.S;
     const int S32 = (int)S;
+    const P* hs[3];
+    const XS* xh[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        hs[s] = p.hin + (int64_t)s * Q * S;
+        xh[s] = p.xin + (int64_t)s * S;
+    }
 
     int nb[Q];
     nb[0] = i;
@@ -441,59 +465,58 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
         load_neighbours<L>(p.nbr, i, nb);
 
     XV xo[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) xo[s] = XV::own_rows(p.xin + (int64_t)s * S, p.xin + (int64_t)(3 + s) * S, i);
-
-    constexpr T wx = T(weight_xplus<L>());
-    T d[3][Q];
-    T dxa[3][2 * DIM + 1];   // X(src) - X_old(x) on the axis links (gradient)
+    T acc[3], qs[3];
+    T dxa[3][2 * DIM];   // X(src) - X_old(x) on the axis links 1 .. 2 DIM
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        d[s][0] = Pop<T, P>::load(p.hin + (int64_t)s * Q * S + i);
-        dxa[s][0] = T(0);
+        xo[s] = XV::own_rows(xh[s], p.xin + (int64_t)(3 + s) * S, i);
+        const T h0 = Pop<T, P>::raw(hs[s] + i);
+        sD[s][0][t] = h0;
+        acc[s] = h0;
+        qs[s] = cb.qout[s] * sc;
     }
+    constexpr T wx = T(weight_xplus<L>());
 #pragma unroll
     for (int k = 1; k < Q; ++k) {
         const int src = nb[k];
         const bool fluid = src >= 0;
         const int hoff = fluid ? k * S32 + src : opp<L>(k) * S32 + i;
         const int xidx = fluid ? src : i;
-        const T oc = (L::e(k, 0) == -1 && src == NB_OUTLET) ? T(weight<L>(opp<L>(k))) / wx : T(0);
+        const bool out = L::e(k, 0) == -1 && src == NB_OUTLET;
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            const T hv = Pop<T, P>::load(p.hin + (int64_t)s * Q * S + hoff);
-            const T dx = xo[s].exch(p.xin[(int64_t)s * S + xidx]);
-            T val = T(weight<L>(k)) * dx + hv;
-            if (L::e(k, 0) == -1) val -= oc * cb.qout[s];
-            d[s][k] = val;
-            if (k <= 2 * DIM) dxa[s][k] = dx;
+            const T dx = xo[s].exch(xh[s][xidx]);
+            T val = T(weight<L>(k) * sc) * dx + Pop<T, P>::raw(hs[s] + hoff);
+            if (L::e(k, 0) == -1) val -= out ? T(weight<L>(opp<L>(k))) / wx * qs[s] : T(0);
+            sD[s][k][t] = val;
+            acc[s] += val;
+            if (k <= 2 * DIM) dxa[s][k - 1] = dx;
         }
     }
-    T X[3], dX[3], g[3][DIM];
+
+    T X[3], g[3][DIM], dXs[3];
     XV xn[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp
-        const T din = cb.xbc[s].minus(xo[s]);
+        // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp, replacing the gathered value
+        const T din = cb.xbc[s].minus(xo[s]) * sc;
 #pragma unroll
-        for (int k = 0; k < Q; ++k) {
-            if (L::e(k, 0) == 1) {
-                const T inl = T(weight<L>(k) + weight<L>(opp<L>(k))) * din - d[s][opp<L>(k)];
-                d[s][k] = nb[k] == NB_INLET ? inl : d[s][k];
+        for (int k = 1; k < Q; ++k) {
+            if (L::e(k, 0) == 1 && nb[k] == NB_INLET) {
+                const T inl = T(weight<L>(k) + weight<L>(opp<L>(k))) * din - sD[s][opp<L>(k)][t];
+                acc[s] += inl - sD[s][k][t];
+                sD[s][k][t] = inl;
             }
         }
 #pragma unroll
         for (int a = 0; a < DIM; ++a) {
             const int kp = 2 + 2 * a, km = 1 + 2 * a;
             const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
-            const T pv = dxa[s][kp], mv = dxa[s][km];
+            const T pv = dxa[s][kp - 1], mv = dxa[s][km - 1];
             g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
         }
-        T acc = T(0);
-#pragma unroll
-        for (int k = 0; k < Q; ++k) acc += d[s][k];
-        dX[s] = acc;
-        xn[s] = xo[s].plus(acc);
+        dXs[s] = acc[s];
+        xn[s] = xo[s].plus(acc[s] * T(1.0 / sc));
         X[s] = xn[s].value();
     }
 
@@ -504,6 +527,7 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
         ms_relax<T, DIM>(X, g[s], J, p.c, s, ts, vs, xinv);
         const T it = Arith<T>::div(T(1), ts);
         const T keep = T(1) - it;
+        const T A = T(3) * sc * X[s] * it;
         P* ho = p.hout + (int64_t)s * Q * S;
         T rest = T(0);
 #pragma unroll
@@ -512,12 +536,12 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
 #pragma unroll
             for (int a = 0; a < DIM; ++a) ev += T(L::e(k, a)) * vs[a];
             const T w = T(weight<L>(k));
-            const T hk = (d[s][k] - w * dX[s]) * keep + T(3) * w * X[s] * ev * it;
-            const P q = Pop<T, P>::quant(hk);
-            rest -= Pop<T, P>::dequant(q);
+            const T hk = (sD[s][k][t] - w * dXs[s]) * keep + (w * A) * ev;
+            const P q = Pop<T, P>::quant_raw(hk);
+            rest -= Pop<T, P>::dequant_raw(q);
             step_store(ho + k * S32 + i, q);
         }
-        step_store(ho + i, Pop<T, P>::quant(rest));
+        step_store(ho + i, Pop<T, P>::quant_raw(rest));
         xn[s].store_rows(p.xout + (int64_t)s * S, p.xout + (int64_t)(3 + s) * S, i);
     }
 }

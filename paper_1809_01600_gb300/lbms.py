@@ -75,7 +75,8 @@ class Info(C.Structure):
                 ("current_A_cm2", C.c_double), ("steps", C.c_int64),
                 ("device_bytes", C.c_size_t), ("h2d_bytes", C.c_uint64),
                 ("d2h_bytes", C.c_uint64), ("n_cases", C.c_int), ("tile_cells", C.c_int),
-                ("tile_min_blocks", C.c_int), ("neighbour_bits", C.c_int)]
+                ("tile_min_blocks", C.c_int), ("neighbour_bits", C.c_int),
+                ("threads_per_cell", C.c_int)]
 
 
 _lib = None

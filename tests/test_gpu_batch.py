@@ -102,6 +102,7 @@ def test_every_step_variant_gives_the_same_fields(L, variant, precision, tol):
         h.step(77)
     i = s.info()
     assert i.neighbour_bits == (16 if 4 <= variant <= 6 else 32)
+    assert i.threads_per_cell == (1 if variant >= 7 else 3)
     assert np.abs(s.fields() - ref.fields()).max() <= tol
 
 
