@@ -33,6 +33,7 @@ WORKLOADS = {
     "anode3d_256x128x128": "anode_3d_256x128x128",
     "anode2d_96x48": "anode_2d_96x48",
     "sweep": None,
+    "table2": None,
 }
 METRIC = "MLUPS/species"
 
@@ -210,6 +211,8 @@ def main():
         return main_reference(args, ws, rank)
     if args.workload == "sweep":
         return main_sweep(args, ws, rank, local)
+    if args.workload == "table2":
+        return main_table2(args, ws, rank, local)
 
     import torch
     if not torch.cuda.is_available():
@@ -364,6 +367,52 @@ def sweep_cases(args):
         for I, x in pts:
             groups[st.dim].append(st.with_(current_A_cm2=I, x_in=x))
     return groups
+
+
+def main_table2(args, ws, rank, local):
+    """The homogenised anode of Section 4.2 (Table 2 gas point): every current
+    of Figs. 2-4 x every inlet dilution in one batch, run to steady state
+    (residual 1e-8, or --time-to-residual) from the uniform inlet start;
+    reports the steady eta - eta_0 table and the time to get it."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1809_01600_gb300 import lbms as L
+    from workloads import cases as W
+    L.load()
+    tol = args.time_to_residual or 1e-8
+    cs = W.paper_table2_cases(64)
+    b = L.Batch.from_cases(cs, precision=args.precision)
+    for k, c in enumerate(cs):
+        b.set_bc(c.x_in, c.current_A_cm2, case=k)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t0 = time.perf_counter()
+    n, steps, r, status = b.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+    eta, _ = b.overpotentials(raise_on_fail=False)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    b.close()
+    nh = len(W.TABLE2_H2)
+    e = np.asarray(eta).reshape(len(W.TABLE2_CURRENTS), nh)
+    table = {f"{I} A/cm2": {f"xH2={xh}": round(float(e[i, j] - e[i, 0]), 6)
+                            for j, xh in enumerate(W.TABLE2_H2) if j > 0}
+             for i, I in enumerate(W.TABLE2_CURRENTS)}
+    nf = sum(c.n_fluid for c in cs)
+    if rank == 0:
+        line = {"metric": "time to residual", "value": round(wall, 3), "unit": "s", "n_gpus": 1,
+                "higher_is_better": False, "vs_baseline": None,
+                "dtype": {"fp32": "f32", "fp64": "f64", "fp16": "f32 (f16 storage)"}[args.precision],
+                "data": "synthetic",
+                "config": {"workload": "homogenised Table 2 anode, 1-D D2Q9 strip nx=64, "
+                                       f"{len(W.TABLE2_CURRENTS)} currents x {nh} inlets in one batch",
+                           "residual": tol, "fluid_cells": nf, "precision": args.precision},
+                "steps": int(n), "steps_per_case": [int(x) for x in steps],
+                "converged": bool(np.all(steps > 0)), "status": int(status),
+                "eta_V_minus_eta0_V": table, "clocks": clk}
+        print(json.dumps(line))
+    return 0
 
 
 def main_sweep(args, ws, rank, local):

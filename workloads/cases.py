@@ -164,3 +164,25 @@ def sweep_operating_points(n: int = 8, seed0: int = 7):
         xh = float(rng.uniform(0.2, 0.8))
         pts.append((I, (xh, xh / 4.0, 1.0 - 1.25 * xh)))
     return pts
+
+
+TABLE2_CURRENTS = (0.3, 0.7, 1.0)            # A/cm2, Figs. 2-4
+TABLE2_H2 = (0.8, 0.6, 0.4, 0.3, 0.2)        # inlet H2 fraction; 0.8 (no Ar) is the eta_0 run
+
+
+def table2_inlet(xh: float) -> tuple:
+    """Inlet composition of Section 4.2: H2:H2O = 4:1 diluted by Ar."""
+    return (xh, xh / 4.0, 1.0 - 1.25 * xh)
+
+
+def paper_table2_cases(nx: int = 64):
+    """The homogenised anode of Section 4.2 (Table 2 gas point, eps/tau =
+    0.46/4.5, d_p = 2.6 um, L = 2 mm) as a 1-D all-fluid D2Q9 strip, for every
+    current of ``TABLE2_CURRENTS`` times every inlet of ``TABLE2_H2``
+    (current-major order)."""
+    out = []
+    for I in TABLE2_CURRENTS:
+        for xh in TABLE2_H2:
+            out.append(open_channel(nx, 1, gas=PAPER_TABLE2, current_A_cm2=I, x_in=table2_inlet(xh),
+                                    name=f"table2_nx{nx}_I{I}_xH2{xh}"))
+    return out
