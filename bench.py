@@ -67,6 +67,18 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(dist, value, device):
+    """The maximum of a per-rank float over every rank of the process group
+    (``dist`` None: a single process, the value itself).  Timings are taken
+    as the slowest replica's."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_case(name):
     from workloads import cases
     return getattr(cases, WORKLOADS[name])()
@@ -255,10 +267,7 @@ def main():
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     t_dev = ms / 1e3
-    if dist:
-        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(dist, t_dev, "cuda")
     units = nf * 3 * args.steps * ws
     value = units / t_dev / 1e6
 
@@ -272,9 +281,11 @@ def main():
                 "frac": round(achieved / peak, 4), "traffic": traffic,
                 "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
                 "algorithmic_bytes_per_launch": nf * bpc,
-                "kernel": "step_kernel<%s,%s>" % ("D3Q19" if case.dim == 3 else "D2Q9",
-                                                 {"fp64": "double,double", "fp32": "float2,float",
-                                                  "fp16": "float2,__half"}[args.precision])}
+                "kernel": "%s<%s, X %s, h %s>" % (
+                    "step_kernel_cell" if tinfo.threads_per_cell == 1 else "step_kernel",
+                    "D3Q19" if case.dim == 3 else "D2Q9",
+                    "double" if args.precision == "fp64" else "float pair",
+                    {"fp64": "double", "fp32": "float", "fp16": "__half"}[args.precision])}
 
     # time to residual from the uniform start (optional): plain FP32 against
     # the chosen form (FP16 storage + slowest-mode extrapolation)
@@ -313,10 +324,7 @@ def main():
         t_e2e = time.perf_counter() - t
         info = s2.info()
         s2.close()
-        if dist:
-            tt = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = float(tt.item())
+        t_e2e = max_over_ranks(dist, t_e2e, "cuda")
         e2e = {"value": round(units / t_e2e / 1e6, 2), "unit": METRIC,
                "h2d_bytes_per_step": int(info.h2d_bytes / args.steps),
                "d2h_bytes_per_step": int(info.d2h_bytes / args.steps),
@@ -458,10 +466,7 @@ def main_sweep(args, ws, rank, local):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     t_dev = ms / 1e3
-    if dist:
-        tt = torch.tensor([t_dev], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(dist, t_dev, "cuda")
     units = nf * 3 * args.steps * ws
     value = units / t_dev / 1e6
     tiles = {dim: "%d cells, %d blocks/SM" % (b.info().tile_cells, b.info().tile_min_blocks)
