@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--time-to-residual", type=float, default=0.0,
                     help="also run to this residual from the uniform start and report the time")
+    ap.add_argument("--ttr-forms", default="",
+                    help="comma list of time-to-residual forms to run (default all): plain_fp32, "
+                         "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--extrapolate-every", type=int, default=20000,
                     help="W of the slowest-mode extrapolation in the accelerated time-to-residual run")
@@ -292,23 +295,29 @@ def main():
     ttr = None
     if args.time_to_residual > 0:
         ttr = {"tol": args.time_to_residual}
-        forms = (("plain_fp32", "fp32", 0), ("fp16_extrapolated", "fp16", args.extrapolate_every),
-                 ("fp32_extrapolated", "fp32", args.extrapolate_every))
-        for label, prec, W in forms:
-            r0 = L.Solver.from_case(case, precision=prec, extrapolate_every=W)
+        forms = (("plain_fp32", "fp32", 0, "uniform"),
+                 ("fp16_extrapolated", "fp16", args.extrapolate_every, "uniform"),
+                 ("fp32_extrapolated", "fp32", args.extrapolate_every, "uniform"),
+                 ("fp16_extrapolated_profile1d", "fp16", args.extrapolate_every, "profile1d"))
+        pick = args.ttr_forms.split(",") if args.ttr_forms else [f[0] for f in forms]
+        for label, prec, W, init in forms:
+            if label not in pick:
+                continue
+            r0 = L.Solver.from_case(case, precision=prec, extrapolate_every=W, init_mode=init)
             r0.set_bc(case.x_in, case.current_A_cm2)
             torch.cuda.synchronize()
             t = time.perf_counter()
             n, r, st = r0.run_to_residual(args.time_to_residual, args.max_steps, raise_on_fail=False)
             ttr_s = time.perf_counter() - t
             eta, _ = r0.overpotential()
-            ttr[label] = {"precision": prec, "extrapolate_every": W, "steps": n, "residual": r,
+            ttr[label] = {"precision": prec, "extrapolate_every": W, "init": init, "steps": n, "residual": r,
                           "seconds": round(ttr_s, 3), "converged": st == L.LBMS_OK, "eta_V": eta}
             r0.close()
-        base = ttr["plain_fp32"]
-        for label in ("fp16_extrapolated", "fp32_extrapolated"):
-            ttr[label]["speedup_vs_plain_fp32"] = round(base["seconds"] / ttr[label]["seconds"], 2)
-            ttr[label]["eta_rel_diff_vs_plain_fp32"] = abs(ttr[label]["eta_V"] - base["eta_V"]) / abs(base["eta_V"])
+        base = ttr.get("plain_fp32")
+        for label, _, _, _ in forms[1:]:
+            if base and label in ttr:
+                ttr[label]["speedup_vs_plain_fp32"] = round(base["seconds"] / ttr[label]["seconds"], 2)
+                ttr[label]["eta_rel_diff_vs_plain_fp32"] = abs(ttr[label]["eta_V"] - base["eta_V"]) / abs(base["eta_V"])
 
     # end to end through the public API with host buffers
     e2e = None

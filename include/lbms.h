@@ -42,6 +42,7 @@ typedef enum {
 
 enum { LBMS_FP64 = 0, LBMS_FP32 = 1, LBMS_FP16 = 2 };
 enum { LBMS_COUPLING_MS = 0, LBMS_COUPLING_TAU_ONLY = 1 };
+enum { LBMS_INIT_UNIFORM = 0, LBMS_INIT_PROFILE_1D = 1 };
 
 /* Geometry.  dim = 2 uses D2Q9 (Eq. 2, weights Eq. 9); dim = 3 uses D3Q19.
  * solid: N bytes, nonzero = solid voxel (half-way bounce-back, Section 3.3).
@@ -100,6 +101,14 @@ typedef struct {
  *             neighbour table by timing; k in 1..8 forces variant k - 1 (for
  *             tests), an unavailable one (16-bit table not built) is an
  *             error [0]
+ *  init_mode  state a case starts from at its first set_bc:
+ *             LBMS_INIT_UNIFORM: the inlet composition everywhere, f = w X_in;
+ *             LBMS_INIT_PROFILE_1D: the initial state of Section 4.1, every
+ *             column x at the 1-D profile of Eq. 19 integrated from the
+ *             inlet with the fluxes held at their outlet values (Eq. 39),
+ *             N_i(x) = N_i|A/E, and the handle's D_ij,eff (Eq. 41);
+ *             LBMS_EDEPLETED from set_bc if that profile drives a mole
+ *             fraction below zero.  Boxes periodic in x start uniform [UNIFORM]
  *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
  *  alloc/free device allocator callbacks (e.g. a framework's caching
  *             allocator); NULL = cudaMalloc/cudaFree [NULL] */
@@ -111,6 +120,7 @@ typedef struct {
     int check_every;
     int extrapolate_every;
     int step_variant;
+    int init_mode;
     void *stream;
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);

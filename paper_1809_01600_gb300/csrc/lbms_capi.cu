@@ -329,6 +329,48 @@ lbms_status upload_field(lbms_ctx* c, int k, const double* X) {
     return LBMS_OK;
 }
 
+// Initial state of Section 4.1: with the fluxes held at their outlet values
+// N_i = -nu_i I / (n F) (Eq. 39) across the anode, Eq. 19 (Gamma = I),
+//   dX_i/dx = sum_{j != i} (X_i N_j - X_j N_i) / (C_t D_ij,eff),
+// is integrated from X_in at x = 0 to every node x_j = j dx (classical
+// fourth-order Runge-Kutta, 16 substeps per node spacing).  prof[s * nx + j].
+// False if a mole fraction goes negative (the current depletes a reactant).
+bool profile_1d(const GasProps& g, const CaseHost& cs, double current, std::vector<double>& prof) {
+    const double I = current * 1.0e4;
+    double N[3];
+    for (int s = 0; s < 3; ++s) N[s] = -g.stoich[s] * I / (g.electrons * kF);
+    auto rhs = [&](const double* X, double* dX) {
+        for (int i = 0; i < 3; ++i) {
+            double v = 0.0;
+            for (int j = 0; j < 3; ++j)
+                if (j != i) v += (X[i] * N[j] - X[j] * N[i]) / (g.C_t * g.D_eff[i][j]);
+            dX[i] = v;
+        }
+    };
+    constexpr int kSub = 16;
+    const double h = cs.dx / kSub;
+    prof.assign(3 * (size_t)cs.nx, 0.0);
+    double X[3] = {cs.x_in[0], cs.x_in[1], cs.x_in[2]};
+    for (int j = 0; j < cs.nx; ++j) {
+        for (int s = 0; s < 3; ++s) {
+            if (!(X[s] >= 0.0)) return false;
+            prof[(size_t)s * cs.nx + j] = X[s];
+        }
+        for (int m = 0; m < kSub && j + 1 < cs.nx; ++m) {
+            double k1[3], k2[3], k3[3], k4[3], t[3];
+            rhs(X, k1);
+            for (int s = 0; s < 3; ++s) t[s] = X[s] + 0.5 * h * k1[s];
+            rhs(t, k2);
+            for (int s = 0; s < 3; ++s) t[s] = X[s] + 0.5 * h * k2[s];
+            rhs(t, k3);
+            for (int s = 0; s < 3; ++s) t[s] = X[s] + h * k3[s];
+            rhs(t, k4);
+            for (int s = 0; s < 3; ++s) X[s] += h / 6.0 * (k1[s] + 2.0 * k2[s] + 2.0 * k3[s] + k4[s]);
+        }
+    }
+    return true;
+}
+
 lbms_status set_case_bc(lbms_ctx* c, int k, const double* x_inlet, double current) {
     lbms_status st = validate_bc(c, x_inlet, current);
     if (st != LBMS_OK) return st;
@@ -347,7 +389,18 @@ lbms_status set_case_bc(lbms_ctx* c, int k, const double* x_inlet, double curren
     if (st != LBMS_OK) return st;
     if (!cs.has_bc) {
         std::vector<double> X(3 * (size_t)cs.N, 0.0);
-        for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * cs.N, X.begin() + (s + 1) * cs.N, cs.x_in[s]);
+        if (c->opt.init_mode == LBMS_INIT_PROFILE_1D && !cs.periodic_x) {
+            std::vector<double> prof;
+            if (!profile_1d(c->gas, cs, current, prof))
+                return fail(c, LBMS_EDEPLETED, "the 1-D initial profile of case %d drives a mole fraction below zero", k);
+            const int64_t plane = (int64_t)cs.ny * cs.nz;
+            for (int s = 0; s < 3; ++s)
+                for (int64_t r = 0; r < plane; ++r)
+                    std::copy(prof.begin() + (size_t)s * cs.nx, prof.begin() + (size_t)(s + 1) * cs.nx,
+                              X.begin() + s * cs.N + r * cs.nx);
+        } else {
+            for (int s = 0; s < 3; ++s) std::fill(X.begin() + s * cs.N, X.begin() + (s + 1) * cs.N, cs.x_in[s]);
+        }
         st = upload_field(c, k, X.data());
         if (st != LBMS_OK) return st;
         cs.has_bc = true;
@@ -570,6 +623,8 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     if (c->opt.check_every <= 0) c->opt.check_every = 100;
     if (c->opt.extrapolate_every < 0) c->opt.extrapolate_every = 0;
     if (c->opt.step_variant < 0 || c->opt.step_variant > kStepVariants) return bail(fail(c, LBMS_EINVAL, "step_variant out of range"));
+    if (c->opt.init_mode != LBMS_INIT_UNIFORM && c->opt.init_mode != LBMS_INIT_PROFILE_1D)
+        return bail(fail(c, LBMS_EINVAL, "init_mode must be LBMS_INIT_UNIFORM or LBMS_INIT_PROFILE_1D"));
     if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
     if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
