@@ -54,6 +54,9 @@ def parse():
                     help="comma list of time-to-residual forms to run (default all): plain_fp32, "
                          "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
+    ap.add_argument("--step-variant", type=int, default=0,
+                    help="0: the autotuner picks the step kernel; k > 0 forces variant k - 1 "
+                         "(to profile the variant a plain run picked)")
     ap.add_argument("--extrapolate-every", type=int, default=20000,
                     help="W of the slowest-mode extrapolation in the accelerated time-to-residual run")
     ap.add_argument("--sweep-2d", type=int, default=8, help="2-D microstructures of the sweep")
@@ -168,9 +171,15 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(workload, precision):
-    """DRAM bytes per launch of the step kernel from the committed ncu summary,
-    valid only while the kernel sources are unchanged."""
+def variant_key(info):
+    """Step-kernel variant as written in profiles/traffic.txt: cells per block
+    x resident blocks, threads per cell, neighbour-index bits."""
+    return f"{info.tile_cells}x{info.tile_min_blocks}/t{info.threads_per_cell}/nb{info.neighbour_bits}"
+
+
+def ncu_traffic(workload, precision, variant):
+    """DRAM bytes per launch of the step kernel variant in use, from the
+    committed ncu summary; valid only while the kernel sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(p).read().splitlines()
@@ -181,7 +190,8 @@ def ncu_traffic(workload, precision):
         if ln.startswith("#") or not ln.strip():
             continue
         kv = dict(x.split("=", 1) for x in ln.split() if "=" in x)
-        if kv.get("kernel_sha") == sha and kv.get("workload") == workload and kv.get("precision") == precision:
+        if (kv.get("kernel_sha") == sha and kv.get("workload") == workload and kv.get("precision") == precision
+                and kv.get("variant") == variant):
             return float(kv["dram_bytes_per_launch"])
     return None
 
@@ -243,7 +253,7 @@ def main():
 
     case = make_case(args.workload)
     nf = case.n_fluid
-    s = L.Solver.from_case(case, precision=args.precision)
+    s = L.Solver.from_case(case, precision=args.precision, step_variant=args.step_variant)
     s.set_bc(case.x_in, case.current_A_cm2)
     stream = torch.cuda.current_stream()
     tinfo = s.info()
@@ -279,10 +289,10 @@ def main():
     per_launch = t_dev / args.steps
     achieved = nf * bpc / per_launch / 1e9
     peak, peak_kind = measured_peak_hbm()
-    traffic = ncu_traffic(case.name, args.precision)
+    traffic = ncu_traffic(case.name, args.precision, variant_key(tinfo))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic,
-                "peak_source": peak_kind, "bytes_per_fluid_cell": bpc,
+                "peak_source": peak_kind, "bytes_per_fluid_cell": bpc, "variant": variant_key(tinfo),
                 "algorithmic_bytes_per_launch": nf * bpc,
                 "kernel": "%s<%s, X %s, h %s>" % (
                     "step_kernel_cell" if tinfo.threads_per_cell == 1 else "step_kernel",
@@ -324,7 +334,7 @@ def main():
     if not args.no_e2e:
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s2 = L.Solver.from_case(case, precision=args.precision)
+        s2 = L.Solver.from_case(case, precision=args.precision, step_variant=args.step_variant)
         s2.set_bc(case.x_in, case.current_A_cm2)
         s2.step(args.steps)
         X = s2.fields()

@@ -212,6 +212,7 @@ struct StepParams {
     const CaseBC<XS>* __restrict__ cases;
     const int* __restrict__ blk_case;   // case of each block of W cells
     int64_t S;
+    int pf_dist;                        // cells ahead to prefetch into L2 (0 = off)
     MsConst<typename Xv<XS>::T> c;
 };
 
@@ -427,6 +428,46 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
     xn.store_rows(p.xout + (int64_t)s * S, p.xout + (int64_t)(3 + s) * S, i);
 }
 
+// L2 prefetch for the 32 cells starting at wb (a warp's cells a fraction of
+// a wave of resident blocks ahead): their neighbour rows and, with 16-bit
+// populations, their own populations and mole fractions.  The warp that
+// steps those cells later finds its first, dependent loads in L2 instead of
+// HBM.  Measured on the 256x128x128 anode: with FP16 populations the full
+// prefetch an eighth of a wave ahead saves 8 %; with FP32 populations
+// prefetching the populations costs up to 25 % (half a wave ahead) while the
+// neighbour rows alone gain about 1 %, so FP32 / FP64 prefetch only those.
+// Prefetches load nothing into registers and are issued only for addresses
+// inside the buffers (wb + 32 <= S).
+__device__ __forceinline__ void prefetch_l2(const void* a) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+}
+
+template <typename P>
+constexpr int prefetch_wave_divisor() {
+    return sizeof(P) == 2 ? 8 : 4;
+}
+
+template <class L, typename XS, typename P, typename NBT>
+__device__ __forceinline__ void prefetch_ahead(const StepParams<XS, P, NBT>& p, int64_t wb, int lane) {
+    if (wb + 32 > p.S) return;
+    constexpr int Q = L::Q;
+    if constexpr (sizeof(P) == 2) {
+        constexpr int XROWS = sizeof(XS) == 8 ? 3 : 6;    // FP64 X, or hi and lo rows
+        constexpr int HB = 32 * (int)sizeof(P);            // bytes of one row segment
+        constexpr int XB = 32 * (int)sizeof(XS);
+        for (int r = lane; r < 3 * Q + XROWS; r += 32) {
+            const char* a = r < 3 * Q ? reinterpret_cast<const char*>(p.hin + (int64_t)r * p.S + wb)
+                                      : reinterpret_cast<const char*>(p.xin + (int64_t)(r - 3 * Q) * p.S + wb);
+            const int nb = r < 3 * Q ? HB : XB;
+            for (int o = 0; o < nb; o += 128) prefetch_l2(a + o);
+        }
+    }
+    constexpr int NW = sizeof(NBT) == 2 ? nb16_width<L>() : nb_width<L>();
+    constexpr int NBYTES = 32 * NW * (int)sizeof(NBT);
+    const char* nbase = reinterpret_cast<const char*>(p.nbr + wb * NW);
+    for (int o = lane * 128; o < NBYTES; o += 32 * 128) prefetch_l2(nbase + o);
+}
+
 // -------------------------------------------------------------------------
 // The same time step with one thread per fluid cell handling all three
 // species: the neighbour decode and the address selection of every link are
@@ -449,6 +490,7 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
     const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
     const int64_t S = p.S;
     const int S32 = (int)S;
+    if (p.pf_dist > 0) prefetch_ahead<L, XS, P, NBT>(p, i - (t & 31) + p.pf_dist, t & 31);
     const P* hs[3];
     const XS* xh[3];
 #pragma unroll

@@ -76,6 +76,8 @@ cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
     p.cases = static_cast<const CaseBC<XS>*>(L.b.cases);
     p.blk_case = L.b.blk_case[variant];
     p.S = L.S;
+    // L2 prefetch distance: a fraction of a wave of resident blocks (per-cell kernel only)
+    p.pf_dist = PER_CELL ? L.sm_count * MB * W / prefetch_wave_divisor<P>() : 0;
     p.c = make_const<T>(L);
     if constexpr (PER_CELL)
         step_kernel_cell<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], W, 0, st>>>(p);
