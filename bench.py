@@ -34,6 +34,7 @@ WORKLOADS = {
     "anode2d_96x48": "anode_2d_96x48",
     "sweep": None,
     "table2": None,
+    "warmstart": None,
 }
 METRIC = "MLUPS/species"
 
@@ -63,6 +64,9 @@ def parse():
     ap.add_argument("--sweep-3d", type=int, default=8, help="3-D microstructures of the sweep")
     ap.add_argument("--sweep-scale", type=float, default=1.0, help="size factor of the sweep grids")
     ap.add_argument("--sweep-points", type=int, default=8, help="operating points per microstructure")
+    ap.add_argument("--ws-train", type=int, default=64, help="warm start: training anodes")
+    ap.add_argument("--ws-test", type=int, default=16, help="warm start: held-out anodes")
+    ap.add_argument("--ws-iters", type=int, default=2000, help="warm start: Adam steps")
     return ap.parse_args()
 
 
@@ -238,6 +242,8 @@ def main():
         return main_sweep(args, ws, rank, local)
     if args.workload == "table2":
         return main_table2(args, ws, rank, local)
+    if args.workload == "warmstart":
+        return main_warmstart(args, ws, rank, local)
 
     import torch
     if not torch.cuda.is_available():
@@ -394,6 +400,77 @@ def sweep_cases(args):
         for I, x in pts:
             groups[st.dim].append(st.with_(current_A_cm2=I, x_in=x))
     return groups
+
+
+def main_warmstart(args, ws, rank, local):
+    """Learned warm start: steady states of seeded 64x32x32 anodes from the
+    batched solver train the network; on held-out anodes, the steps to
+    residual 1e-8 from the uniform start, the 1-D profile of Section 4.1 and
+    the network's prediction (plain FP32, and FP16 storage + extrapolation)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1809_01600_gb300 import lbms as L
+    from workloads import cases as W
+    L.load()
+    tol = args.time_to_residual or 1e-8
+    train = W.warmstart_cases(args.ws_train, 1000)
+    test = W.warmstart_cases(args.ws_test, 5000)
+    out = {"residual": tol}
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = L.Batch.from_cases(train, precision="fp32", extrapolate_every=5000)
+    for k, c in enumerate(train):
+        b.set_bc(c.x_in, c.current_A_cm2, case=k)
+    n, _, _, st = b.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+    net = L.Net(width=704, depth=3, seed=1)
+    for k in range(len(train)):
+        net.add_sample(b, k)
+    b.close()
+    t1 = time.perf_counter()
+    loss = net.train(args.ws_iters, batch=8192, lr=1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    out["data"] = {"cases": len(train), "rows": net.info()[1], "steps": int(n), "seconds": round(t1 - t0, 2)}
+    out["training"] = {"params": net.info()[0], "iters": args.ws_iters, "batch": 8192,
+                       "final_loss": loss, "seconds": round(t2 - t1, 2)}
+
+    forms = (("plain_fp32", "fp32", 0), ("fp16_extrapolated", "fp16", 5000))
+    for label, prec, Wx in forms:
+        res = {}
+        for start in ("uniform", "profile1d", "network"):
+            bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx,
+                                    init_mode="profile1d" if start == "profile1d" else "uniform")
+            for k, c in enumerate(test):
+                bt.set_bc(c.x_in, c.current_A_cm2, case=k)
+            torch.cuda.synchronize()
+            ta = time.perf_counter()
+            if start == "network":
+                for k in range(len(test)):
+                    net.warm_start(bt, k)
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
+            n, steps, r, st = bt.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
+            res[start] = {"mean_steps": float(np.mean(steps)), "max_steps": int(np.max(steps)),
+                          "converged": bool(np.all(steps > 0)), "start_seconds": round(tb - ta, 3),
+                          "batch_seconds": round(tc - tb, 2)}
+            bt.close()
+        for start in ("profile1d", "network"):
+            res[start]["steps_vs_uniform"] = round(res[start]["mean_steps"] / res["uniform"]["mean_steps"], 3)
+        out[label] = res
+    net.close()
+    if rank == 0:
+        v = out["plain_fp32"]["network"]["mean_steps"]
+        line = {"metric": "steps to residual (held-out anodes, network start)", "value": v, "unit": "steps",
+                "n_gpus": 1, "higher_is_better": False, "vs_baseline": None, "dtype": "bf16 network, f32 LBM",
+                "data": "synthetic",
+                "config": {"workload": f"learned warm start, {len(train)} training + {len(test)} held-out "
+                                       f"64x32x32 D3Q19 anodes"},
+                "warm_start": out}
+        print(json.dumps(line))
+    return 0
 
 
 def main_table2(args, ws, rank, local):

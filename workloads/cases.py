@@ -186,3 +186,21 @@ def paper_table2_cases(nx: int = 64):
             out.append(open_channel(nx, 1, gas=PAPER_TABLE2, current_A_cm2=I, x_in=table2_inlet(xh),
                                     name=f"table2_nx{nx}_I{I}_xH2{xh}"))
     return out
+
+
+def warmstart_cases(n: int, seed0: int, shape=(32, 32, 64)):
+    """Anodes for the learned warm start, sampled in the style of the
+    batched sweep at one grid size: spheres of radius 2-4, porosity
+    U(0.35, 0.50), current U(0.25, 1.5) A/cm2, inlet H2 U(0.3, 0.8) at
+    H2:H2O = 4:1 with Ar the balance; case k uses seed seed0 + k."""
+    out = []
+    for k in range(n):
+        rng = np.random.Generator(np.random.PCG64(seed0 + k))
+        por = float(rng.uniform(0.35, 0.50))
+        rad = int(rng.integers(2, 5))
+        I = float(rng.uniform(0.25, 1.5))
+        xh = float(rng.uniform(0.3, 0.8))
+        out.append(porous(shape, radius=rad, porosity=por, seed=seed0 + k, current_A_cm2=I,
+                          x_in=(xh, xh / 4.0, 1.0 - 1.25 * xh),
+                          name=f"ws{seed0 + k}_{'x'.join(map(str, shape[::-1]))}_eps{por:.2f}_r{rad}"))
+    return out
