@@ -66,7 +66,8 @@ def parse():
     ap.add_argument("--sweep-points", type=int, default=8, help="operating points per microstructure")
     ap.add_argument("--ws-train", type=int, default=64, help="warm start: training anodes")
     ap.add_argument("--ws-test", type=int, default=16, help="warm start: held-out anodes")
-    ap.add_argument("--ws-iters", type=int, default=2000, help="warm start: Adam steps")
+    ap.add_argument("--ws-iters", type=int, default=4000, help="warm start: Adam steps")
+    ap.add_argument("--ws-lr", type=float, default=1e-3, help="warm start: peak learning rate")
     return ap.parse_args()
 
 
@@ -428,11 +429,11 @@ def main_warmstart(args, ws, rank, local):
         net.add_sample(b, k)
     b.close()
     t1 = time.perf_counter()
-    loss = net.train(args.ws_iters, batch=8192, lr=1e-3)
+    loss = net.train(args.ws_iters, batch=8192, lr=args.ws_lr)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     out["data"] = {"cases": len(train), "rows": net.info()[1], "steps": int(n), "seconds": round(t1 - t0, 2)}
-    out["training"] = {"params": net.info()[0], "iters": args.ws_iters, "batch": 8192,
+    out["training"] = {"params": net.info()[0], "iters": args.ws_iters, "batch": 8192, "lr": args.ws_lr,
                        "final_loss": loss, "seconds": round(t2 - t1, 2)}
 
     forms = (("plain_fp32", "fp32", 0), ("fp16_extrapolated", "fp16", 5000))

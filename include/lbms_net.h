@@ -1,0 +1,88 @@
+/* Learned warm start for the LBM iteration.
+ *
+ * The LBM of arXiv:1809.01600 is iterated from an initial state to the
+ * steady state (Section 4.1 starts it from a 1-D profile; lbms.h offers that
+ * profile as LBMS_INIT_PROFILE_1D).  The steady state does not depend on the
+ * start, so a better start only shortens the iteration.  This network
+ * predicts that steady state from the anode's geometry and boundary data;
+ * the LBM then iterates from the prediction to the same residual as from any
+ * other start, and stays the judge of the result.  The paper has no network:
+ * this is an addition on top of its method.
+ *
+ * Model: a pointwise multilayer perceptron.  Every fluid cell gets a feature
+ * row built on the GPU from the solid mask and the boundary data: the
+ * Section 4.1 profile at its x, x / L, the fluid fraction of cubes of
+ * half-width 1, 3 and 7 cells around it, the cross-section porosity at x and
+ * the cumulative resistance int_0^x dx / porosity(x) (normalised), the
+ * current density and the inlet composition.  The network maps the row to
+ * 100 (X_steady - X_profile) for the three species.  Hidden layers use ReLU;
+ * weights are stored in BF16 for the tensor-core matrix products (FP32
+ * accumulation) with FP32 master copies updated by Adam.
+ *
+ * All functions return an lbms_status and never abort; buffers are host
+ * memory owned by the caller unless stated otherwise.  A net is not thread
+ * safe; its device work runs on the legacy default stream. */
+#ifndef LBMS_NET_H
+#define LBMS_NET_H
+
+#include <stdint.h>
+
+#include "lbms.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbms_net lbms_net;
+
+enum { LBMS_NET_FEATURES = 64 };   /* feature row width (16 used, zero padded) */
+
+/* width: hidden units per layer (multiple of 64, 64..2048); depth: hidden
+ * layers (1..8).  Weights are drawn from a counter-based generator
+ * (SplitMix64) keyed by seed; the output layer starts at zero. */
+lbms_status lbms_net_create(int width, int depth, uint64_t seed, lbms_net **out);
+
+/* Adds one case of a handle as training data: the feature rows of its fluid
+ * cells and, as the target, the handle's current mole fractions of that case
+ * (call it on a steady state).  The case must have boundary data. */
+lbms_status lbms_net_add_sample(lbms_net *net, lbms_ctx *ctx, int case_index);
+
+/* iters steps of Adam (beta 0.9 / 0.999, eps 1e-8) on mean-square error over
+ * batches of `batch` rows (a multiple of 64) drawn uniformly with replacement
+ * from the training rows by a counter-based generator; the learning rate
+ * decays from lr by a cosine to lr / 20 over the iterations of this call.
+ * last_loss (may be NULL) receives the mean loss of the last 10 steps. */
+lbms_status lbms_net_train(lbms_net *net, int iters, int batch, double lr, double *last_loss);
+
+/* Predicts the steady mole fractions of one case of a handle and restarts
+ * that case from them (f = w X, as lbms_batch_set_fields).  The prediction
+ * is clamped to X >= 1e-6 and renormalised to sum 1 per cell.  X (may be
+ * NULL) receives the predicted dense field [3][N] (0 in solid cells). */
+lbms_status lbms_net_warm_start(lbms_net *net, lbms_ctx *ctx, int case_index, double *X);
+
+/* Inference and one training step on caller-given rows, for tests:
+ * features [rows][LBMS_NET_FEATURES] as BF16 bit patterns, targets
+ * [rows][3]; rows a multiple of 64.  out [rows][3] receives the network
+ * output (before the step).  With lr = 0 the parameters do not change;
+ * the gradients are kept for lbms_net_get. */
+lbms_status lbms_net_forward(lbms_net *net, const uint16_t *features, int rows, float *out);
+lbms_status lbms_net_train_batch(lbms_net *net, const uint16_t *features, const float *targets, int rows,
+                                 double lr, double *loss);
+
+/* Parameters and gradients, layer by layer: for layer l (0 = input layer,
+ * depth = output layer) W_l [out_l][in_l] row-major then b_l [out_l], with
+ * in_0 = LBMS_NET_FEATURES, out_depth = 3 and every other size = width.
+ * what: 0 = FP32 master parameters, 1 = gradients of the last step.
+ * n = number of floats the buffer holds (lbms_net_info's n_params). */
+lbms_status lbms_net_get(const lbms_net *net, int what, float *buf, int64_t n);
+lbms_status lbms_net_set(lbms_net *net, const float *params, int64_t n);
+
+lbms_status lbms_net_info(const lbms_net *net, int64_t *n_params, int64_t *n_samples);
+const char *lbms_net_last_error(const lbms_net *net);
+void lbms_net_destroy(lbms_net *net);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif

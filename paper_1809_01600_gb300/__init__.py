@@ -5,6 +5,6 @@ Maxwell-Stefan equations through a local relaxation time (arXiv:1809.01600).
 The compute path is the CUDA library built from ``csrc/`` (C ABI in
 ``include/lbms.h``); ``lbms.Solver`` is its Python binding.
 """
-from .lbms import Batch, LbmsError, Solver, load  # noqa: F401
+from .lbms import Batch, LbmsError, Net, Solver, load  # noqa: F401
 
-__all__ = ["Solver", "Batch", "LbmsError", "load"]
+__all__ = ["Solver", "Batch", "Net", "LbmsError", "load"]

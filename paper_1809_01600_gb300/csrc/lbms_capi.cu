@@ -572,6 +572,33 @@ lbms_status extrap_check(lbms_ctx* c, Extrapolator& ex) {
 
 }  // namespace
 
+namespace lbms {
+
+bool case_view(const lbms_ctx* c, int k, CaseView* v) {
+    if (!c || k < 0 || k >= (int)c->cases.size() || !v) return false;
+    const CaseHost& cs = c->cases[k];
+    v->nx = cs.nx;
+    v->ny = cs.ny;
+    v->nz = cs.nz;
+    v->N = cs.N;
+    v->nf = cs.nf;
+    v->fluid_cell = cs.fluid_cell.data();
+    for (int s = 0; s < 3; ++s) v->x_in[s] = cs.x_in[s];
+    v->current = cs.current;
+    v->periodic_x = cs.periodic_x != 0;
+    v->has_bc = cs.has_bc;
+    return true;
+}
+
+bool case_profile_1d(const lbms_ctx* c, int k, std::vector<double>& prof) {
+    if (!c || k < 0 || k >= (int)c->cases.size()) return false;
+    const CaseHost& cs = c->cases[k];
+    if (cs.periodic_x) return false;
+    return profile_1d(c->gas, cs, cs.current, prof);
+}
+
+}  // namespace lbms
+
 extern "C" {
 
 void lbms_default_options(lbms_options* o) {

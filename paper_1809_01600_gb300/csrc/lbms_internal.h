@@ -4,7 +4,10 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
+
+struct lbms_ctx;
 
 namespace lbms {
 
@@ -83,5 +86,23 @@ cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st);
 // per-case sums of (X - E)^2 etc. into case_out[c * 10 + v], E unchanged
 cudaError_t launch_case_extrap_norms(const Launch& L, cudaStream_t st);
 cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st);
+
+// Read-only view of one case of a handle (for the warm-start network).
+struct CaseView {
+    int nx, ny, nz;
+    int64_t N;                    // cells of the dense grid
+    int nf;                       // fluid cells
+    const int64_t* fluid_cell;    // dense index of each fluid cell (host)
+    double x_in[3];
+    double current;               // A/cm2
+    bool periodic_x;
+    bool has_bc;
+};
+// False if k is out of range.
+bool case_view(const lbms_ctx* c, int k, CaseView* v);
+// The initial profile of Section 4.1 for case k at its current boundary
+// data, prof[s * nx + x]; false if it goes negative (or the box is periodic
+// in x).
+bool case_profile_1d(const lbms_ctx* c, int k, std::vector<double>& prof);
 
 }  // namespace lbms

@@ -32,6 +32,9 @@ EXPORTS = ("lbms_default_options", "lbms_create", "lbms_set_bc", "lbms_set_field
            "lbms_last_error", "lbms_status_string", "lbms_residual_sums_noalloc",
            "lbms_create_batch", "lbms_batch_set_bc", "lbms_batch_set_fields", "lbms_batch_residuals",
            "lbms_batch_run_to_residual", "lbms_batch_get_fields", "lbms_batch_overpotentials")
+NET_EXPORTS = ("lbms_net_create", "lbms_net_add_sample", "lbms_net_train", "lbms_net_warm_start",
+               "lbms_net_forward", "lbms_net_train_batch", "lbms_net_get", "lbms_net_set", "lbms_net_info",
+               "lbms_net_last_error", "lbms_net_destroy")
 
 
 class LbmsError(RuntimeError):
@@ -123,6 +126,17 @@ def load(build_if_needed: bool = True):
         "lbms_batch_run_to_residual": (st, [P, C.c_double, I64, C.POINTER(I64), C.POINTER(I64), D]),
         "lbms_batch_get_fields": (st, [P, C.c_int, D, D, D]),
         "lbms_batch_overpotentials": (st, [P, D, D]),
+        "lbms_net_create": (st, [C.c_int, C.c_int, C.c_uint64, C.POINTER(P)]),
+        "lbms_net_add_sample": (st, [P, P, C.c_int]),
+        "lbms_net_train": (st, [P, C.c_int, C.c_int, C.c_double, D]),
+        "lbms_net_warm_start": (st, [P, P, C.c_int, D]),
+        "lbms_net_forward": (st, [P, P, C.c_int, P]),
+        "lbms_net_train_batch": (st, [P, P, P, C.c_int, C.c_double, D]),
+        "lbms_net_get": (st, [P, C.c_int, P, I64]),
+        "lbms_net_set": (st, [P, P, I64]),
+        "lbms_net_info": (st, [P, C.POINTER(I64), C.POINTER(I64)]),
+        "lbms_net_last_error": (C.c_char_p, [P]),
+        "lbms_net_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -429,3 +443,101 @@ class Solver(_Handle):
         self._check(self._lib.lbms_boundary_flux(self._h, _dptr(fl), _dptr(tot)))
         return fl, tot
 
+
+
+def to_bf16_bits(a):
+    """Float array -> BF16 bit patterns (uint16), round to nearest even."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    r = ((u >> 16) & 1) + 0x7FFF
+    return ((u + r) >> 16).astype(np.uint16)
+
+
+def from_bf16_bits(b):
+    return (np.asarray(b, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+class Net:
+    """The warm-start network of include/lbms_net.h (argument marshalling only)."""
+
+    FEATURES = 64
+
+    def __init__(self, width=704, depth=3, seed=0):
+        self._lib = load()
+        h = C.c_void_p()
+        s = self._lib.lbms_net_create(int(width), int(depth), int(seed), C.byref(h))
+        if s != LBMS_OK:
+            raise LbmsError(s, "lbms_net_create(width=%d, depth=%d)" % (width, depth))
+        self._h = h
+        self.width, self.depth = width, depth
+
+    def _check(self, s):
+        if s != LBMS_OK:
+            raise LbmsError(s, self._lib.lbms_net_last_error(self._h).decode())
+
+    def info(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self._lib.lbms_net_info(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def add_sample(self, handle, case=0):
+        self._check(self._lib.lbms_net_add_sample(self._h, handle._h, int(case)))
+
+    def train(self, iters, batch=8192, lr=1e-3):
+        loss = C.c_double()
+        self._check(self._lib.lbms_net_train(self._h, int(iters), int(batch), float(lr), C.byref(loss)))
+        return loss.value
+
+    def warm_start(self, handle, case=0):
+        shape = handle.shapes[case] if hasattr(handle, "shapes") else handle.shape
+        X = np.empty((3,) + tuple(shape))
+        self._check(self._lib.lbms_net_warm_start(self._h, handle._h, int(case), _dptr(X)))
+        return X
+
+    def forward(self, features):
+        f = np.ascontiguousarray(features, dtype=np.uint16)
+        rows = f.shape[0]
+        out = np.empty((rows, 3), dtype=np.float32)
+        self._check(self._lib.lbms_net_forward(self._h, f.ctypes.data, rows, out.ctypes.data))
+        return out
+
+    def train_batch(self, features, targets, lr=0.0):
+        f = np.ascontiguousarray(features, dtype=np.uint16)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        loss = C.c_double()
+        self._check(self._lib.lbms_net_train_batch(self._h, f.ctypes.data, t.ctypes.data, f.shape[0],
+                                                   float(lr), C.byref(loss)))
+        return loss.value
+
+    def _layers(self, flat):
+        """Splits a flat parameter vector into [(W, b), ...] per layer."""
+        out, off = [], 0
+        dims = [self.FEATURES] + [self.width] * self.depth + [3]
+        for l in range(self.depth + 1):
+            i, o = dims[l], dims[l + 1]
+            W = flat[off:off + o * i].reshape(o, i)
+            off += o * i
+            b = flat[off:off + o]
+            off += o
+            out.append((W, b))
+        return out
+
+    def get(self, what=0):
+        n, _ = self.info()
+        buf = np.empty(n, dtype=np.float32)
+        self._check(self._lib.lbms_net_get(self._h, int(what), buf.ctypes.data, n))
+        return self._layers(buf)
+
+    def set(self, layers):
+        flat = np.concatenate([np.concatenate([W.ravel(), b.ravel()]) for W, b in layers]).astype(np.float32)
+        self._check(self._lib.lbms_net_set(self._h, flat.ctypes.data, flat.size))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbms_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -9,11 +9,13 @@ import pytest
 
 from paper_1809_01600_gb300 import lbms as L
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbms.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+HEADER = os.path.join(INCLUDE, "lbms.h")
+NET_HEADER = os.path.join(INCLUDE, "lbms_net.h")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(path=HEADER):
+    text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(lbms_[a-z_]+)\s*\(", text)))
 
@@ -25,6 +27,23 @@ def test_every_declared_symbol_is_exported():
     for n in names:
         assert hasattr(lib, n), n
     assert set(names) == set(L.EXPORTS)
+
+
+def test_every_network_symbol_is_exported():
+    lib = L.load()
+    names = declared_functions(NET_HEADER)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.NET_EXPORTS)
+
+
+def test_bf16_conversion_round_trip():
+    x = np.array([0.0, 1.0, -2.5, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -9, 3.0e-3], dtype=np.float32)
+    y = L.from_bf16_bits(L.to_bf16_bits(x))
+    assert y[0] == 0.0 and y[1] == 1.0 and y[2] == -2.5
+    assert y[3] == 1.0                      # tie to even
+    assert y[4] == 1.0 + 2 ** -7            # rounds up
+    assert abs(y[5] / x[5] - 1.0) < 2 ** -8
 
 
 def test_default_options_and_status_strings():
