@@ -32,6 +32,7 @@ import numpy as np  # noqa: E402
 WORKLOADS = {
     "anode3d_256x128x128": "anode_3d_256x128x128",
     "anode2d_96x48": "anode_2d_96x48",
+    "anode3d_512": "anode_3d_512",
     "sweep": None,
     "table2": None,
     "warmstart": None,

@@ -99,6 +99,12 @@ def anode_3d_256x128x128() -> Case:
                   name="anode3d_256x128x128_r3_eps0.40", current_A_cm2=1.0)
 
 
+def anode_3d_512() -> Case:
+    """3-D D3Q19 512^3 anode: spheres r = 4, porosity 0.40, seed 7, 1.0 A/cm2."""
+    return porous((512, 512, 512), radius=4, porosity=0.40, seed=7,
+                  name="anode3d_512x512x512_r4_eps0.40", current_A_cm2=1.0)
+
+
 def anode_3d_small(nx=40, ny=24, nz=20, radius=3, porosity=0.40, seed=2,
                    current=1.0) -> Case:
     """Reduced 3-D anode with the same recipe, for oracle-sized parity runs."""
