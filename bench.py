@@ -171,7 +171,7 @@ def measured_peak_hbm():
 
 def kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("lbms_kernels.cuh", "lbms_lattice.cuh", "lbms_launch.cu"):
+    for f in ("lbms_kernels.cuh", "lbms_lattice.cuh", "lbms_launch.cu", "lbms_step_launch.cuh"):
         with open(os.path.join(ROOT, "paper_1809_01600_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -43,6 +43,8 @@ typedef enum {
 enum { LBMS_FP64 = 0, LBMS_FP32 = 1, LBMS_FP16 = 2 };
 enum { LBMS_COUPLING_MS = 0, LBMS_COUPLING_TAU_ONLY = 1 };
 enum { LBMS_INIT_UNIFORM = 0, LBMS_INIT_PROFILE_1D = 1 };
+enum { LBMS_OUTLET_FLUX = 0, LBMS_OUTLET_EXTRAPOLATED = 1 };
+enum { LBMS_GRAD_CENTRAL = 0, LBMS_GRAD_FORWARD = 1 };
 
 /* Geometry.  dim = 2 uses D2Q9 (Eq. 2, weights Eq. 9); dim = 3 uses D3Q19.
  * solid: N bytes, nonzero = solid voxel (half-way bounce-back, Section 3.3).
@@ -109,6 +111,18 @@ typedef struct {
  *             N_i(x) = N_i|A/E, and the handle's D_ij,eff (Eq. 41);
  *             LBMS_EDEPLETED from set_bc if that profile drives a mole
  *             fraction below zero.  Boxes periodic in x start uniform [UNIFORM]
+ *  outlet_bc  LBMS_OUTLET_FLUX: the Eq. 39 flux imposed link-wise at x =
+ *             nx-1, f_k = f*_opp - (w_opp / W) q (exactly q leaves per node
+ *             and step; Ar sees bounce-back); LBMS_OUTLET_EXTRAPOLATED: Eq. 37
+ *             read as a wet node, X_out = X^{t-1}(nx-2) + dX with dX from
+ *             Eq. 19 over one spacing at the Eq. 39 fluxes, applied with the
+ *             Eq. 36 rule (first order: the delivered flux approaches q as
+ *             dx -> 0); computed by the per-cell step kernel only, so the
+ *             autotuner then picks among variants 6-7 [FLUX]
+ *  grad_stencil  LBMS_GRAD_CENTRAL: central differences of the previous
+ *             step's X on every axis (one-sided at x = 0, nx-1);
+ *             LBMS_GRAD_FORWARD: Eq. 35 as printed, the forward difference
+ *             along x only [CENTRAL]
  *  stream     cudaStream_t for all device work, NULL = legacy default [NULL]
  *  alloc/free device allocator callbacks (e.g. a framework's caching
  *             allocator); NULL = cudaMalloc/cudaFree [NULL] */
@@ -121,6 +135,8 @@ typedef struct {
     int extrapolate_every;
     int step_variant;
     int init_mode;
+    int outlet_bc;
+    int grad_stencil;
     void *stream;
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);

@@ -16,16 +16,23 @@ One time step t (all quantities in lattice units, c_s^2 = 1/3):
    Outlet x = nx-1, for e_ax = -1 (Eq. 39 flux imposed link-wise):
    f_a = f*_abar - (w_abar / W) q, W = sum of w over e_x = +1 links, q the
    lattice image of N_i = -nu_i I/(nF); this removes exactly q per node per
-   step (zero for Ar).
+   step (zero for Ar).  outlet_bc="extrapolated" instead reads Eq. 37 as a
+   wet node: X_out = X^{t-1}(nx-2) + dX with dX from Eq. 19 over one
+   spacing at the outlet fluxes, dX_i = sum_j (X_i q_j - X_j q_i) / D_ij
+   (X at nx-2, or at the node itself where nx-2 is solid), applied with the
+   Eq. 36 rule f_a = (w_a + w_abar) X_out - f_abar.
 2. Moments: X_i = sum_a f_a (the zeroth moment of Eq. 29's distribution).
 3. Gradient of the stored field of the previous step (Eq. 35, read as a
    central difference on every axis): (X(x+e) - X(x-e))/2; a solid
    neighbour takes the centre value (mirror about the half-way wall); at the
    x = 0 / x = nx-1 nodes the one-sided difference is used.
+   grad_stencil="forward" takes Eq. 35 literally: X(x+1) - X(x) along x
+   only (backward at x = nx-1), zero along y and z.
 4. Maxwell-Stefan coupling with species 3 (Ar) as the reference n:
    B from Eq. 32, J = -B^-1 grad X per axis (Eqs. 31, 33, 34 with
-   Gamma = I, Eq. 30 ideal gas), J_3 = -J_1 - J_2 (Eq. 21 with u_M = 0,
-   Section 3.1), N = J (Eq. 20).
+   Gamma = I, Eq. 30 ideal gas); J_3 from the n-th row of Eq. 19 given
+   J_1, J_2 (not from the closure of Eq. 21, which leaves sum X - 1 without
+   a restoring term); N = J (Eq. 20, u_M = 0, Section 3.1).
 5. Effective diffusivity, Eq. 24, with the paper's rule that each flux
    points as its stoichiometric coefficient says (Section 3.1) and its
    observation that the fluxes across the thin anode stay at their A/E values
@@ -63,7 +70,8 @@ V_MAX = 0.1           # bound on |v_i| (lattice units)
 
 
 class Oracle:
-    def __init__(self, case, tau_min=1.0, tau_max=5.0, coupling="ms", dt=None):
+    def __init__(self, case, tau_min=1.0, tau_max=5.0, coupling="ms", dt=None,
+                 grad_stencil="central", outlet_bc="flux"):
         self.case = case
         self.solid = np.asarray(case.solid, dtype=bool)
         self.fluid = ~self.solid
@@ -80,6 +88,10 @@ class Oracle:
         self.tau_min = tau_min
         self.tau_max = tau_max
         self.coupling = coupling
+        if grad_stencil not in ("central", "forward") or outlet_bc not in ("flux", "extrapolated"):
+            raise ValueError("grad_stencil: central | forward; outlet_bc: flux | extrapolated")
+        self.grad_stencil = grad_stencil
+        self.outlet_bc = outlet_bc
         self.t = 0
         self.init()
 
@@ -131,9 +143,23 @@ class Oracle:
                 if E[a, 0] == 1:
                     P[:, a, :, :, 0] = ((W[a] + W[b]) * self.x_in[:, None, None]
                                         - P[:, b, :, :, 0])
-                elif E[a, 0] == -1:
+                elif E[a, 0] == -1 and self.outlet_bc == "flux":
                     P[:, a, :, :, nx - 1] = (A[:, b, :, :, nx - 1]
                                              - (W[b] / w_out) * q[:, None, None])
+            if self.outlet_bc == "extrapolated":
+                Dl = self.sc.D_lat
+                Xn = np.where(self.solid[None, :, :, nx - 2], self.Xprev[:, :, :, nx - 1],
+                              self.Xprev[:, :, :, nx - 2])
+                dX = np.zeros_like(Xn)
+                for i in range(3):
+                    for j in range(3):
+                        if j != i:
+                            dX[i] += (Xn[i] * q[j] - Xn[j] * q[i]) / Dl[i, j]
+                Xout = Xn + dX
+                for a in range(self.Q):
+                    if E[a, 0] == -1:
+                        b = opp[a]
+                        P[:, a, :, :, nx - 1] = (W[a] + W[b]) * Xout - P[:, b, :, :, nx - 1]
         P[:, :, self.solid] = 0.0
         return P
 
@@ -153,6 +179,10 @@ class Oracle:
             else:
                 has_p = np.ones((1, 1, 1), bool)
                 has_m = np.ones((1, 1, 1), bool)
+            if self.grad_stencil == "forward":
+                if a == 0:
+                    G[:, a] = np.where(has_p, p - Xp, np.where(has_m, Xp - m, 0.0))
+                continue
             G[:, a] = np.where(has_p & has_m, 0.5 * (p - m),
                                np.where(has_p, p - Xp, np.where(has_m, Xp - m, 0.0)))
         return G

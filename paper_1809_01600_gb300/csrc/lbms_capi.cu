@@ -280,10 +280,11 @@ lbms_status autotune(lbms_ctx* c) {
     CK(cudaEventCreate(&e0), "autotune event");
     CK(cudaEventCreate(&e1), "autotune event");
     float best = std::numeric_limits<float>::infinity();
-    int pick = 0;
+    int pick = L.outlet_extrap ? 6 : 0;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < kStepVariants && e == cudaSuccess; ++v) {
         if (kVariantNb16[v] && !L.b.nbr16) continue;
+        if (L.outlet_extrap && !kVariantPerCell[v]) continue;   // the per-cell kernel alone has it
         e = launch_step_variant(L, v, c->stream);  // warm-up
         if (e != cudaSuccess) break;
         e = cudaEventRecord(e0, c->stream);
@@ -652,6 +653,13 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     if (c->opt.step_variant < 0 || c->opt.step_variant > kStepVariants) return bail(fail(c, LBMS_EINVAL, "step_variant out of range"));
     if (c->opt.init_mode != LBMS_INIT_UNIFORM && c->opt.init_mode != LBMS_INIT_PROFILE_1D)
         return bail(fail(c, LBMS_EINVAL, "init_mode must be LBMS_INIT_UNIFORM or LBMS_INIT_PROFILE_1D"));
+    if (c->opt.outlet_bc != LBMS_OUTLET_FLUX && c->opt.outlet_bc != LBMS_OUTLET_EXTRAPOLATED)
+        return bail(fail(c, LBMS_EINVAL, "outlet_bc must be LBMS_OUTLET_FLUX or LBMS_OUTLET_EXTRAPOLATED"));
+    if (c->opt.grad_stencil != LBMS_GRAD_CENTRAL && c->opt.grad_stencil != LBMS_GRAD_FORWARD)
+        return bail(fail(c, LBMS_EINVAL, "grad_stencil must be LBMS_GRAD_CENTRAL or LBMS_GRAD_FORWARD"));
+    if (c->opt.outlet_bc == LBMS_OUTLET_EXTRAPOLATED && c->opt.step_variant > 0 &&
+        !kVariantPerCell[c->opt.step_variant - 1])
+        return bail(fail(c, LBMS_EINVAL, "the extrapolated outlet needs a per-cell step variant (7 or 8)"));
     if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
     if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
@@ -747,6 +755,8 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     L.tau_min = c->opt.tau_min;
     L.tau_max = c->opt.tau_max;
     L.drift = c->opt.coupling == LBMS_COUPLING_MS ? 1 : 0;
+    L.grad_forward = c->opt.grad_stencil == LBMS_GRAD_FORWARD ? 1 : 0;
+    L.outlet_extrap = c->opt.outlet_bc == LBMS_OUTLET_EXTRAPOLATED ? 1 : 0;
 
     // reduction segments and block -> case tables
     std::vector<int2> segs, case_segs(n_cases), case_rows(n_cases);

@@ -59,6 +59,8 @@ struct Launch {
     double stoich[3] = {-1, 1, 0};     // nu_i of the electrode reaction (Eq. 38)
     double tau_min = 1.0, tau_max = 5.0;
     int drift = 1;
+    int grad_forward = 0;              // Eq. 35 forward difference along x only
+    int outlet_extrap = 0;             // extrapolated wet-node outlet (per-cell step kernel only)
     int sm_count = 152;
 };
 
@@ -79,6 +81,8 @@ void pack_case_bc(int precision, const CaseHostBC& h, void* dst);  // host-side 
 
 cudaError_t launch_step(const Launch& L, cudaStream_t st);
 cudaError_t launch_step_variant(const Launch& L, int variant, cudaStream_t st);
+// the same with the grad_forward / outlet_extrap options compiled in
+cudaError_t launch_step_variant_literal(const Launch& L, int variant, cudaStream_t st);
 cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st);
 cudaError_t launch_fields(const Launch& L, cudaStream_t st);
 cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st);

@@ -47,7 +47,22 @@ struct MsConst {
     int reacting[3];      // nu_i != 0 (Eq. 24 applies); 0: inert, mixture value
     T tau_min, tau_max;
     int drift;            // 1: drift velocity carries the Maxwell-Stefan flux tau does not
+    int grad_forward;     // 1: Eq. 35 literally (forward difference along x only)
+    int outlet_extrap;    // 1: outlet as an extrapolated wet node (Eq. 37 reading), per-cell kernel only
 };
+
+// One component of the lagged gradient (Eq. 35) from the differences to the
+// +e_a and -e_a neighbours (pv, mv; 0 for a solid neighbour, the mirror about
+// the half-way wall) and whether those neighbours are cells of the grid
+// (hp, hm; false beyond the inlet and outlet columns).  Central differences
+// on every axis, one-sided at x = 0 and x = nx-1; with `forward`, Eq. 35 as
+// printed: the forward difference along x (backward at x = nx-1) and no
+// y / z component.
+template <typename T>
+__device__ __forceinline__ T grad_component(bool hp, bool hm, T pv, T mv, int a, int forward) {
+    if (forward) return a == 0 ? (hp ? pv : (hm ? -mv : T(0))) : T(0);
+    return (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+}
 
 // Neighbour row of cell i: nb[k] for k = 1..Q-1 (nb[0] is left to the caller).
 template <class L>
@@ -312,8 +327,10 @@ __device__ __forceinline__ void ms_relax(const T (&X)[3], const T (&gs)[DIM], co
 // one per (species, cell); warps are species-uniform, so every load and store
 // of a warp walks consecutive cells of one species row.  The three threads of
 // a cell meet once, through shared memory, to exchange X and its gradient for
-// the coupling (which needs all species).
-template <class L, typename XS, typename P, typename NBT, int W, int MB>
+// the coupling (which needs all species).  LIT = false compiles the default
+// readings only (central gradient, flux outlet); LIT = true also honours the
+// grad_forward / outlet_extrap options of MsConst.
+template <class L, typename XS, typename P, typename NBT, int W, int MB, bool LIT>
 __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P, NBT> p) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
@@ -384,7 +401,7 @@ __global__ void __launch_bounds__(3 * W, MB) step_kernel(const StepParams<XS, P,
             const int km = 1 + 2 * a;   // source of +e_a: the cell at x - e_a
             const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
             const T pv = dxs[kp], mv = dxs[km];   // solid neighbour -> mirror (0)
-            sG[s][a][c] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+            sG[s][a][c] = grad_component(hp, hm, pv, mv, a, LIT ? p.c.grad_forward : 0);
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) dX += d[k];
@@ -477,7 +494,7 @@ __device__ __forceinline__ void prefetch_ahead(const StepParams<XS, P, NBT>& p, 
 // low enough for a useful number of resident warps.  Everything from the
 // gather to the store runs in storage units (h * kStore), so the FP16
 // scaling costs one multiply per species instead of one per population.
-template <class L, typename XS, typename P, typename NBT, int W, int MB>
+template <class L, typename XS, typename P, typename NBT, int W, int MB, bool LIT>
 __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P, NBT> p) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
@@ -515,7 +532,7 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
         const T h0 = Pop<T, P>::raw(hs[s] + i);
         sD[s][0][t] = h0;
         acc[s] = h0;
-        qs[s] = cb.qout[s] * sc;
+        qs[s] = (LIT && p.c.outlet_extrap) ? T(0) : cb.qout[s] * sc;
     }
     constexpr T wx = T(weight_xplus<L>());
 #pragma unroll
@@ -536,10 +553,42 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
         }
     }
 
+    bool at_outlet = false;
+#pragma unroll
+    for (int k = 1; k < Q; ++k)
+        if (L::e(k, 0) == -1) at_outlet = at_outlet || nb[k] == NB_OUTLET;
+
     T X[3], g[3][DIM], dXs[3];
     XV xn[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
+        // Extrapolated outlet (Eq. 37 read as a wet node): X_out = X^{t-1}(x-1)
+        // + dX, dX_s = sum_j (X_s q_j - X_j q_s) / D_sj (Eq. 19 over one
+        // spacing at the outlet fluxes), with X at x - 1 (link 1 pulls from
+        // there; the cell's own X where x - 1 is solid, whose difference is 0),
+        // then the Eq. 36 rule on the links entering from beyond the outlet.
+        if (LIT && p.c.outlet_extrap && at_outlet) {
+            T Xn[3];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) Xn[r] = xo[r].value() + dxa[r][0];
+            const T q0 = cb.qout[0], q1 = cb.qout[1], q2 = cb.qout[2];
+            T dX;
+            if (s == 0)
+                dX = (Xn[0] * q1 - Xn[1] * q0) * p.c.i12 + (Xn[0] * q2 - Xn[2] * q0) * p.c.i13;
+            else if (s == 1)
+                dX = (Xn[1] * q0 - Xn[0] * q1) * p.c.i12 + (Xn[1] * q2 - Xn[2] * q1) * p.c.i23;
+            else
+                dX = (Xn[2] * q0 - Xn[0] * q2) * p.c.i13 + (Xn[2] * q1 - Xn[1] * q2) * p.c.i23;
+            const T xod = (dxa[s][0] + dX) * sc;   // (X_out - X_old(x)) in storage units
+#pragma unroll
+            for (int k = 1; k < Q; ++k) {
+                if (L::e(k, 0) == -1 && nb[k] == NB_OUTLET) {
+                    const T v = T(weight<L>(k) + weight<L>(opp<L>(k))) * xod - sD[s][opp<L>(k)][t];
+                    acc[s] += v - sD[s][k][t];
+                    sD[s][k][t] = v;
+                }
+            }
+        }
         // inlet (Eq. 36): f_k = (w_k + w_opp) X_in - f_opp, replacing the gathered value
         const T din = cb.xbc[s].minus(xo[s]) * sc;
 #pragma unroll
@@ -555,7 +604,7 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
             const int kp = 2 + 2 * a, km = 1 + 2 * a;
             const bool hp = nb[kp] >= NB_SOLID, hm = nb[km] >= NB_SOLID;
             const T pv = dxa[s][kp - 1], mv = dxa[s][km - 1];
-            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+            g[s][a] = grad_component(hp, hm, pv, mv, a, LIT ? p.c.grad_forward : 0);
         }
         dXs[s] = acc[s];
         xn[s] = xo[s].plus(acc[s] * T(1.0 / sc));
@@ -616,7 +665,7 @@ __global__ void fields_kernel(const XS* __restrict__ xcur, const XS* __restrict_
             const bool hp = cp >= NB_SOLID, hm = cm >= NB_SOLID;
             const T pv = cp >= 0 ? xo.exch(XV::nb(xprev, S, s, cp)) : T(0);
             const T mv = cm >= 0 ? xo.exch(XV::nb(xprev, S, s, cm)) : T(0);
-            g[s][a] = (hp && hm) ? T(0.5) * (pv - mv) : (hp ? pv : (hm ? -mv : T(0)));
+            g[s][a] = grad_component(hp, hm, pv, mv, a, c.grad_forward);
         }
     }
 #pragma unroll

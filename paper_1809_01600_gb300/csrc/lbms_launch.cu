@@ -8,38 +8,15 @@
 
 #include "lbms_internal.h"
 #include "lbms_kernels.cuh"
+#include "lbms_step_launch.cuh"
 
 namespace lbms {
+
+using launch_detail::make_const;
 
 namespace {
 
 constexpr int kBlock = 256;
-
-template <typename T>
-MsConst<T> make_const(const Launch& L) {
-    MsConst<T> c;
-    const double Dl[3][3] = {{0.0, L.D12, L.D13}, {L.D12, 0.0, L.D23}, {L.D13, L.D23, 0.0}};
-    c.i12 = T(1.0 / L.D12);
-    c.i13 = T(1.0 / L.D13);
-    c.i23 = T(1.0 / L.D23);
-    for (int i = 0; i < 3; ++i) {
-        // Eq. 24 with N_j / N_i = nu_j / nu_i: 1/D_i = sum_{j!=i} (X_j - X_i nu_j / nu_i) / D_ij
-        c.reacting[i] = L.stoich[i] != 0.0 ? 1 : 0;
-        double hs = 0.0, aii = 0.0;
-        for (int j = 0; j < 3; ++j) {
-            if (j == i) continue;
-            c.a[i][j] = T(1.0 / Dl[i][j]);
-            hs += 0.5 / Dl[i][j];
-            if (c.reacting[i]) aii -= (L.stoich[j] / L.stoich[i]) / Dl[i][j];
-        }
-        c.a[i][i] = T(aii);
-        c.h[i] = T(hs);
-    }
-    c.tau_min = T(L.tau_min);
-    c.tau_max = T(L.tau_max);
-    c.drift = L.drift;
-    return c;
-}
 
 inline void to_x(double v, Xv<double>& out) { out.v = v; }
 inline void to_x(double v, Xv<float>& out) {
@@ -58,48 +35,6 @@ void pack_t(const CaseHostBC& h, void* dst) {
     c.base = h.base;
     c.nf = h.nf;
     std::memcpy(dst, &c, sizeof(c));
-}
-
-template <class Lat, typename XS, typename P, typename NBT, int W, int MB, bool PER_CELL = false>
-cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
-    using T = typename Xv<XS>::T;
-    StepParams<XS, P, NBT> p;
-    p.hin = static_cast<const P*>(L.b.f[L.cur]);
-    p.hout = static_cast<P*>(L.b.f[L.cur ^ 1]);
-    p.xin = static_cast<const XS*>(L.b.X[L.cur]);
-    p.xout = static_cast<XS*>(L.b.X[L.cur ^ 1]);
-    if constexpr (sizeof(NBT) == 2)
-        p.nbr = L.b.nbr16;
-    else
-        p.nbr = L.b.nbr;
-    p.nbr32 = L.b.nbr;
-    p.cases = static_cast<const CaseBC<XS>*>(L.b.cases);
-    p.blk_case = L.b.blk_case[variant];
-    p.S = L.S;
-    // L2 prefetch distance: a fraction of a wave of resident blocks (per-cell kernel only)
-    p.pf_dist = PER_CELL ? L.sm_count * MB * W / prefetch_wave_divisor<P>() : 0;
-    p.c = make_const<T>(L);
-    if constexpr (PER_CELL)
-        step_kernel_cell<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], W, 0, st>>>(p);
-    else
-        step_kernel<Lat, XS, P, NBT, W, MB><<<L.nblk[variant], 3 * W, 0, st>>>(p);
-    return cudaGetLastError();
-}
-
-template <class Lat, typename XS, typename P>
-cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
-    static_assert(kStepVariants == 8 && kVariantPerCell[6] && kVariantPerCell[7] && !kVariantPerCell[5],
-                  "variant table");
-    switch (variant) {
-        case 0: return step_w<Lat, XS, P, int, kVariantCells[0], kVariantMinBlocks[0]>(L, 0, st);
-        case 1: return step_w<Lat, XS, P, int, kVariantCells[1], kVariantMinBlocks[1]>(L, 1, st);
-        case 2: return step_w<Lat, XS, P, int, kVariantCells[2], kVariantMinBlocks[2]>(L, 2, st);
-        case 3: return step_w<Lat, XS, P, int16_t, kVariantCells[3], kVariantMinBlocks[3]>(L, 3, st);
-        case 4: return step_w<Lat, XS, P, int16_t, kVariantCells[4], kVariantMinBlocks[4]>(L, 4, st);
-        case 5: return step_w<Lat, XS, P, int16_t, kVariantCells[5], kVariantMinBlocks[5]>(L, 5, st);
-        case 6: return step_w<Lat, XS, P, int, kVariantCells[6], kVariantMinBlocks[6], true>(L, 6, st);
-        default: return step_w<Lat, XS, P, int, kVariantCells[7], kVariantMinBlocks[7], true>(L, 7, st);
-    }
 }
 
 template <class Lat, typename XS, typename P>
@@ -189,7 +124,9 @@ void pack_case_bc(int precision, const CaseHostBC& h, void* dst) {
     } while (0)
 
 cudaError_t launch_step_variant(const Launch& L, int variant, cudaStream_t st) {
-    LBMS_DISPATCH(step_t, L, variant, st);
+    using launch_detail::step_t;
+    if (L.grad_forward || L.outlet_extrap) return launch_step_variant_literal(L, variant, st);
+    LBMS_STEP_DISPATCH(false);
 }
 cudaError_t launch_step(const Launch& L, cudaStream_t st) { return launch_step_variant(L, L.variant, st); }
 cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st) {

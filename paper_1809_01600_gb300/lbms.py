@@ -21,6 +21,10 @@ LBMS_FP64, LBMS_FP32, LBMS_FP16 = 0, 1, 2
 LBMS_COUPLING_MS, LBMS_COUPLING_TAU_ONLY = 0, 1
 LBMS_INIT_UNIFORM, LBMS_INIT_PROFILE_1D = 0, 1
 _INIT_MODES = {"uniform": LBMS_INIT_UNIFORM, "profile1d": LBMS_INIT_PROFILE_1D}
+LBMS_OUTLET_FLUX, LBMS_OUTLET_EXTRAPOLATED = 0, 1
+LBMS_GRAD_CENTRAL, LBMS_GRAD_FORWARD = 0, 1
+_OUTLETS = {"flux": LBMS_OUTLET_FLUX, "extrapolated": LBMS_OUTLET_EXTRAPOLATED}
+_STENCILS = {"central": LBMS_GRAD_CENTRAL, "forward": LBMS_GRAD_FORWARD}
 
 STATUS_NAMES = {0: "LBMS_OK", 1: "LBMS_EINVAL", 2: "LBMS_ENOMEM", 3: "LBMS_ECUDA",
                 4: "LBMS_ENOTCONVERGED", 5: "LBMS_EUNSTABLE", 6: "LBMS_EDEPLETED",
@@ -68,7 +72,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("coupling", C.c_int), ("tau_min", C.c_double),
                 ("tau_max", C.c_double), ("dt_s", C.c_double), ("check_every", C.c_int),
                 ("extrapolate_every", C.c_int), ("step_variant", C.c_int),
-                ("init_mode", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("init_mode", C.c_int), ("outlet_bc", C.c_int), ("grad_stencil", C.c_int),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", C.c_void_p)]
 
 
@@ -155,7 +160,8 @@ class _Handle:
 
     def _setup(self, molar_mass, fuller_volume, stoich, electrons, D_binary, pore_diameter,
                eps_over_tau, precision, coupling, tau_min, tau_max, dt, check_every, stream,
-               torch_allocator, extrapolate_every=0, step_variant=0, init_mode="uniform"):
+               torch_allocator, extrapolate_every=0, step_variant=0, init_mode="uniform",
+               outlet_bc="flux", grad_stencil="central"):
         lib = load()
         self._lib = lib
         self._mm = np.ascontiguousarray(molar_mass, dtype=np.float64)
@@ -180,6 +186,8 @@ class _Handle:
         o.extrapolate_every = int(extrapolate_every)
         o.step_variant = int(step_variant)
         o.init_mode = _INIT_MODES[init_mode]
+        o.outlet_bc = _OUTLETS[outlet_bc]
+        o.grad_stencil = _STENCILS[grad_stencil]
         self._keep = []
         if stream is None or torch_allocator:
             try:
@@ -273,13 +281,13 @@ class Batch(_Handle):
     def __init__(self, solids, dim=None, length_x=2e-3, periodic_x=False, *, T=1073.0, p=101325.0,
                  precision="fp32", coupling="ms", tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100,
                  stream=None, torch_allocator=True, extrapolate_every=0, step_variant=0,
-                 init_mode="uniform", **gas):
+                 init_mode="uniform", outlet_bc="flux", grad_stencil="central", **gas):
         g = dict(_GAS_DEFAULTS)
         g.update(gas)
         sp, df, o = self._setup(g["molar_mass"], g["fuller_volume"], g["stoich"], g["electrons"],
                                 g["D_binary"], g["pore_diameter"], g["eps_over_tau"], precision,
                                 coupling, tau_min, tau_max, dt, check_every, stream, torch_allocator,
-                                extrapolate_every, step_variant, init_mode)
+                                extrapolate_every, step_variant, init_mode, outlet_bc, grad_stencil)
         n = len(solids)
         lx = list(length_x) if np.ndim(length_x) else [length_x] * n
         px = list(periodic_x) if np.ndim(periodic_x) else [periodic_x] * n
@@ -366,11 +374,12 @@ class Solver(_Handle):
                  stoich=(-1, 1, 0), electrons=2, D_binary=None, pore_diameter=1e-6,
                  eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
                  tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
-                 torch_allocator=True, extrapolate_every=0, step_variant=0, init_mode="uniform"):
+                 torch_allocator=True, extrapolate_every=0, step_variant=0, init_mode="uniform",
+                 outlet_bc="flux", grad_stencil="central"):
         sp, df, o = self._setup(molar_mass, fuller_volume, stoich, electrons, D_binary,
                                 pore_diameter, eps_over_tau, precision, coupling, tau_min, tau_max,
                                 dt, check_every, stream, torch_allocator, extrapolate_every,
-                                step_variant, init_mode)
+                                step_variant, init_mode, outlet_bc, grad_stencil)
         g, mask, shape, dim = self._geometry(solid, dim, length_x, periodic_x)
         self._mask = mask
         self.shape = shape

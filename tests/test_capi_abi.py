@@ -94,6 +94,9 @@ def _create(geom_kw=None, species_kw=None, T=1073.0, p=101325.0, opt_kw=None, ma
     (None, None, {"opt_kw": {"tau_min": 0.4}}, "tau_min"),
     (None, None, {"opt_kw": {"coupling": 3}}, "coupling"),
     (None, None, {"opt_kw": {"init_mode": 2}}, "init_mode"),
+    (None, None, {"opt_kw": {"outlet_bc": 2}}, "outlet_bc"),
+    (None, None, {"opt_kw": {"grad_stencil": 2}}, "grad_stencil"),
+    (None, None, {"opt_kw": {"outlet_bc": 1, "step_variant": 1}}, "per-cell"),
 ])
 def test_create_rejects_invalid_input(geom_kw, species_kw, extra, needle):
     s, h, msg = _create(geom_kw, species_kw, **extra)

@@ -291,3 +291,44 @@ def test_mirror_and_transpose_symmetry_3d():
         om = Oracle(c.with_(solid=np.ascontiguousarray(solid)))
         om.step(80)
         assert np.abs(o.X - back(om.X)).max() < 1e-13
+
+
+# ------------------------- the literal readings of Eqs. 35 and 37 (options)
+def _order_1d(grad_stencil, outlet_bc):
+    errs, flux = [], []
+    for nx in (9, 17, 33):
+        c = cases.open_channel(nx, 1, current_A_cm2=1.0, length_x=2e-3)
+        o = Oracle(c, grad_stencil=grad_stencil, outlet_bc=outlet_bc)
+        sc = o.sc
+        Xc = ternary_1d(np.arange(nx) * sc.dx, c.x_in, sc.N_out[0], sc.C_t,
+                        sc.D_eff[0, 1], sc.D_eff[0, 2], sc.D_eff[1, 2])
+        o.init(Xc[:, None, None, :])
+        n, r = o.run_to_residual(1e-12, 400000, 100)
+        assert r <= 1e-12
+        k = (nx - 1) // 8
+        errs.append(np.abs(o.X[:, 0, 0, :] - Xc)[:, ::k].max())
+        flux.append(np.abs(o.plane_flux()[0] / sc.q_lat[0] - 1.0).max())
+    return np.array(errs), np.array(flux)
+
+
+@pytest.mark.slow
+def test_forward_gradient_stencil_is_first_order():
+    """Eq. 35 as printed (forward difference, x only): the 1-D anode still
+    converges to the closed form, at first order, and the flux condition
+    (Eq. 39) still holds exactly."""
+    errs, flux = _order_1d("forward", "flux")
+    ratios = errs[:-1] / errs[1:]
+    assert np.all((ratios > 1.7) & (ratios < 2.3))
+    assert flux.max() < 1e-8
+
+
+@pytest.mark.slow
+def test_extrapolated_outlet_is_first_order():
+    """Eq. 37 read as a wet node: first-order convergence to the closed form,
+    and the delivered outlet flux approaches Eq. 39's as dx halves."""
+    errs, flux = _order_1d("central", "extrapolated")
+    ratios = errs[:-1] / errs[1:]
+    assert np.all((ratios > 1.7) & (ratios < 2.3))
+    fr = flux[:-1] / flux[1:]
+    assert np.all((fr > 1.7) & (fr < 2.3))
+    assert flux[-1] < 1e-4
