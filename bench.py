@@ -54,7 +54,8 @@ def parse():
                     help="also run to this residual from the uniform start and report the time")
     ap.add_argument("--ttr-forms", default="",
                     help="comma list of time-to-residual forms to run (default all): plain_fp32, "
-                         "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d")
+                         "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d, "
+                         "fp16_extrapolated_network")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--step-variant", type=int, default=0,
                     help="0: the autotuner picks the step kernel; k > 0 forces variant k - 1 "
@@ -316,21 +317,33 @@ def main():
         forms = (("plain_fp32", "fp32", 0, "uniform"),
                  ("fp16_extrapolated", "fp16", args.extrapolate_every, "uniform"),
                  ("fp32_extrapolated", "fp32", args.extrapolate_every, "uniform"),
-                 ("fp16_extrapolated_profile1d", "fp16", args.extrapolate_every, "profile1d"))
+                 ("fp16_extrapolated_profile1d", "fp16", args.extrapolate_every, "profile1d"),
+                 ("fp16_extrapolated_network", "fp16", args.extrapolate_every, "network"))
         pick = args.ttr_forms.split(",") if args.ttr_forms else [f[0] for f in forms]
+        net = None
+        if "fp16_extrapolated_network" in pick:
+            from workloads import cases as W_
+            net, info = train_warmstart_net(L, W_.warmstart_cases(args.ws_train, 1000), 1e-8, args)
+            ttr["network"] = dict(info, note="trained on 64x32x32 anodes; the prediction time is inside "
+                                             "the form's seconds, the training is not")
         for label, prec, W, init in forms:
             if label not in pick:
                 continue
-            r0 = L.Solver.from_case(case, precision=prec, extrapolate_every=W, init_mode=init)
+            r0 = L.Solver.from_case(case, precision=prec, extrapolate_every=W,
+                                    init_mode="uniform" if init == "network" else init)
             r0.set_bc(case.x_in, case.current_A_cm2)
             torch.cuda.synchronize()
             t = time.perf_counter()
+            if init == "network":
+                net.warm_start(r0)
             n, r, st = r0.run_to_residual(args.time_to_residual, args.max_steps, raise_on_fail=False)
             ttr_s = time.perf_counter() - t
             eta, _ = r0.overpotential()
             ttr[label] = {"precision": prec, "extrapolate_every": W, "init": init, "steps": n, "residual": r,
                           "seconds": round(ttr_s, 3), "converged": st == L.LBMS_OK, "eta_V": eta}
             r0.close()
+        if net is not None:
+            net.close()
         base = ttr.get("plain_fp32")
         for label, _, _, _ in forms[1:]:
             if base and label in ttr:
@@ -404,6 +417,30 @@ def sweep_cases(args):
     return groups
 
 
+def train_warmstart_net(L, train, tol, args):
+    """Steady states of the training anodes (one batch, FP32 + extrapolation)
+    and a warm-start network trained on them; returns the net and timings."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = L.Batch.from_cases(train, precision="fp32", extrapolate_every=5000)
+    for k, c in enumerate(train):
+        b.set_bc(c.x_in, c.current_A_cm2, case=k)
+    n, _, _, st = b.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+    net = L.Net(width=704, depth=3, seed=1)
+    for k in range(len(train)):
+        net.add_sample(b, k)
+    b.close()
+    t1 = time.perf_counter()
+    loss = net.train(args.ws_iters, batch=8192, lr=args.ws_lr)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return net, {"data": {"cases": len(train), "rows": net.info()[1], "steps": int(n),
+                          "seconds": round(t1 - t0, 2)},
+                 "training": {"params": net.info()[0], "iters": args.ws_iters, "batch": 8192, "lr": args.ws_lr,
+                              "final_loss": loss, "seconds": round(t2 - t1, 2)}}
+
+
 def main_warmstart(args, ws, rank, local):
     """Learned warm start: steady states of seeded 64x32x32 anodes from the
     batched solver train the network; on held-out anodes, the steps to
@@ -419,23 +456,8 @@ def main_warmstart(args, ws, rank, local):
     test = W.warmstart_cases(args.ws_test, 5000)
     out = {"residual": tol}
 
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    b = L.Batch.from_cases(train, precision="fp32", extrapolate_every=5000)
-    for k, c in enumerate(train):
-        b.set_bc(c.x_in, c.current_A_cm2, case=k)
-    n, _, _, st = b.run_to_residual(tol, args.max_steps, raise_on_fail=False)
-    net = L.Net(width=704, depth=3, seed=1)
-    for k in range(len(train)):
-        net.add_sample(b, k)
-    b.close()
-    t1 = time.perf_counter()
-    loss = net.train(args.ws_iters, batch=8192, lr=args.ws_lr)
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    out["data"] = {"cases": len(train), "rows": net.info()[1], "steps": int(n), "seconds": round(t1 - t0, 2)}
-    out["training"] = {"params": net.info()[0], "iters": args.ws_iters, "batch": 8192, "lr": args.ws_lr,
-                       "final_loss": loss, "seconds": round(t2 - t1, 2)}
+    net, info = train_warmstart_net(L, train, tol, args)
+    out.update(info)
 
     forms = (("plain_fp32", "fp32", 0), ("fp16_extrapolated", "fp16", 5000))
     for label, prec, Wx in forms:
