@@ -6,7 +6,7 @@
  * start, so a better start only shortens the iteration.  This network
  * predicts that steady state from the anode's geometry and boundary data;
  * the LBM then iterates from the prediction to the same residual as from any
- * other start, and stays the judge of the result.  The paper has no network:
+ * other start, and its result is the one that counts.  The paper has no network:
  * this is an addition on top of its method.
  *
  * Model: a pointwise multilayer perceptron.  Every fluid cell gets a feature
