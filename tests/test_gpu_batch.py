@@ -119,3 +119,40 @@ def test_far_links_of_the_16_bit_table(L, variant):
     assert s.info().neighbour_bits == (16 if variant >= 4 else 32)
     f = ~c.solid
     assert np.abs(s.fields() - o.X)[:, f].max() <= 1e-11
+
+
+@pytest.mark.slow
+def test_full_sweep_launch_sampled_cases_against_oracle(L):
+    """The benchmark's batched sweep at full size (8 2-D + 8 3-D seeded
+    microstructures x 8 operating points, 128 cases, ~61M fluid cells, one
+    FP32 launch per lattice and step): two sampled cases - the largest 3-D
+    and the largest 2-D grid - start from non-uniform fields, and after two
+    batched steps every one of their cells matches the oracle run on that
+    case alone."""
+    import bench
+    args = type("A", (), dict(sweep_2d=8, sweep_3d=8, sweep_scale=1.0, sweep_points=8))()
+    groups = bench.sweep_cases(args)
+    for dim in (3, 2):
+        cs = groups[dim]
+        k = int(np.argmax([c.n_cells for c in cs]))
+        b = L.Batch.from_cases(cs, precision="fp32")
+        for j, c in enumerate(cs):
+            b.set_bc(c.x_in, c.current_A_cm2, case=j)
+        c = cs[k]
+        rng = np.random.Generator(np.random.PCG64(90 + dim))
+        nz, ny, nx = c.shape
+        x = np.arange(nx)[None, None, :]
+        y = np.arange(ny)[None, :, None]
+        X0 = np.empty((3,) + c.shape)
+        X0[0] = c.x_in[0] + 0.02 * np.sin(2 * np.pi * x / nx + rng.random()) * np.cos(2 * np.pi * y / ny)
+        X0[2] = c.x_in[2] + 0.01 * np.cos(2 * np.pi * x / nx)
+        X0[1] = 1.0 - X0[0] - X0[2]
+        b.set_fields(k, X0)
+        b.step(2)
+        X = b.fields(k)
+        b.close()
+        o = Oracle(c)
+        o.init(X0)
+        o.step(2)
+        f = ~c.solid
+        assert np.abs(X - o.X)[:, f].max() <= 1e-6, (dim, c.name)
