@@ -53,9 +53,10 @@ def parse():
     ap.add_argument("--time-to-residual", type=float, default=0.0,
                     help="also run to this residual from the uniform start and report the time")
     ap.add_argument("--ttr-forms", default="",
-                    help="comma list of time-to-residual forms to run (default all): plain_fp32, "
+                    help="comma list of time-to-residual forms to run: plain_fp32, plain_fp64, "
                          "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d, "
-                         "fp16_extrapolated_network")
+                         "fp16_extrapolated_network (default: plain_fp32 and the three "
+                         "extrapolated forms without the network)")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--step-variant", type=int, default=0,
                     help="0: the autotuner picks the step kernel; k > 0 forces variant k - 1 "
@@ -315,11 +316,13 @@ def main():
     if args.time_to_residual > 0:
         ttr = {"tol": args.time_to_residual}
         forms = (("plain_fp32", "fp32", 0, "uniform"),
+                 ("plain_fp64", "fp64", 0, "uniform"),
                  ("fp16_extrapolated", "fp16", args.extrapolate_every, "uniform"),
                  ("fp32_extrapolated", "fp32", args.extrapolate_every, "uniform"),
                  ("fp16_extrapolated_profile1d", "fp16", args.extrapolate_every, "profile1d"),
                  ("fp16_extrapolated_network", "fp16", args.extrapolate_every, "network"))
-        pick = args.ttr_forms.split(",") if args.ttr_forms else [f[0] for f in forms]
+        pick = (args.ttr_forms.split(",") if args.ttr_forms
+                else [f[0] for f in forms if f[0] not in ("plain_fp64", "fp16_extrapolated_network")])
         net = None
         if "fp16_extrapolated_network" in pick:
             from workloads import cases as W_
