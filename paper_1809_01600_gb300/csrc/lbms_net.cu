@@ -57,13 +57,33 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+// Four 8x8 BF16 matrices from shared memory; lane l supplies the address of
+// row (l % 8) of matrix l / 8.
+__device__ __forceinline__ void ldsm_x4(uint32_t (&r)[4], const void* smem) {
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(sa));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
 // P[z][M][N] = sum over k in [z kchunk, (z+1) kchunk) of A[m][k] B[n][k].
 // Block: 64 x 64 output tile, 4 warps of 32 x 32; K in steps of 32 staged in
-// shared memory (rows padded to 40 elements: conflict-free fragment reads).
+// shared memory by cp.async, two stages (the next step loads while this one
+// is multiplied); rows padded to 40 elements for conflict-free fragment
+// reads.
 __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
                                                       int ldb, float* __restrict__ P, int M, int N, int kchunk) {
-    __shared__ __align__(16) bf16 sA[kTM][kTK + 8];
-    __shared__ __align__(16) bf16 sB[kTN][kTK + 8];
+    __shared__ __align__(16) bf16 sA[2][kTM][kTK + 8];
+    __shared__ __align__(16) bf16 sB[2][kTN][kTK + 8];
     const int m0 = blockIdx.y * kTM, n0 = blockIdx.x * kTN;
     const int k0 = blockIdx.z * kchunk;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -77,39 +97,49 @@ __global__ void __launch_bounds__(128) gemm_tn_kernel(const bf16* __restrict__ A
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
 
-    for (int kk = k0; kk < k0 + kchunk; kk += kTK) {
-        // 64 rows x 32 elements = 256 chunks of 16 bytes per operand
+    // 64 rows x 32 elements = 256 chunks of 16 bytes per operand and stage
+    auto stage = [&](int buf, int kk) {
         for (int c = threadIdx.x; c < kTM * kTK / 8; c += 128) {
             const int r = c >> 2, q = (c & 3) * 8;
-            *reinterpret_cast<uint4*>(&sA[r][q]) =
-                *reinterpret_cast<const uint4*>(A + (int64_t)(m0 + r) * lda + kk + q);
-            *reinterpret_cast<uint4*>(&sB[r][q]) =
-                *reinterpret_cast<const uint4*>(B + (int64_t)(n0 + r) * ldb + kk + q);
+            cp_async16(&sA[buf][r][q], A + (int64_t)(m0 + r) * lda + kk + q);
+            cp_async16(&sB[buf][r][q], B + (int64_t)(n0 + r) * ldb + kk + q);
+        }
+        cp_async_commit();
+    };
+    const int nk = kchunk / kTK;
+    stage(0, k0);
+    for (int it = 0; it < nk; ++it) {
+        const int buf = it & 1;
+        if (it + 1 < nk) {
+            stage(buf ^ 1, k0 + (it + 1) * kTK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
 #pragma unroll
         for (int ks = 0; ks < kTK; ks += 16) {
+            // A fragments (16 x 16, rows m): matrices (rows 0-7 | 8-15) x (k 0-7 | 8-15);
+            // B fragments of two n-blocks of 8: matrices (n 0-7, k 0-7), (n 0-7, k 8-15),
+            // (n 8-15, k 0-7), (n 8-15, k 8-15), i.e. b[j][0], b[j][1], b[j+1][0], b[j+1][1]
             uint32_t a[2][4], b[4][2];
 #pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const int r = wm + i * 16 + g;
-                a[i][0] = *reinterpret_cast<const uint32_t*>(&sA[r][ks + 2 * t]);
-                a[i][1] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][ks + 2 * t]);
-                a[i][2] = *reinterpret_cast<const uint32_t*>(&sA[r][ks + 8 + 2 * t]);
-                a[i][3] = *reinterpret_cast<const uint32_t*>(&sA[r + 8][ks + 8 + 2 * t]);
-            }
+            for (int i = 0; i < 2; ++i) ldsm_x4(a[i], &sA[buf][wm + i * 16 + (lane & 15)][ks + (lane >> 4) * 8]);
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int r = wn + j * 8 + g;
-                b[j][0] = *reinterpret_cast<const uint32_t*>(&sB[r][ks + 2 * t]);
-                b[j][1] = *reinterpret_cast<const uint32_t*>(&sB[r][ks + 8 + 2 * t]);
+            for (int jj = 0; jj < 2; ++jj) {
+                uint32_t r[4];
+                ldsm_x4(r, &sB[buf][wn + jj * 16 + (lane & 7) + ((lane >> 4) << 3)][ks + ((lane >> 3) & 1) * 8]);
+                b[2 * jj][0] = r[0];
+                b[2 * jj][1] = r[1];
+                b[2 * jj + 1][0] = r[2];
+                b[2 * jj + 1][1] = r[3];
             }
 #pragma unroll
             for (int i = 0; i < 2; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a[i], b[j]);
         }
-        __syncthreads();
+        __syncthreads();   // the stage just read is refilled two steps later
     }
     float* Pz = P + (int64_t)blockIdx.z * M * N;
 #pragma unroll
