@@ -102,6 +102,21 @@ void* dev_alloc(lbms_ctx* c, size_t bytes) {
     return p;
 }
 
+// Releases one allocation of dev_alloc before the handle's end.
+void dev_free(lbms_ctx* c, void* p) {
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (c->allocs[k].first != p) continue;
+        cudaStreamSynchronize(c->stream);
+        if (c->opt.free)
+            c->opt.free(p, c->allocs[k].second, c->stream, c->opt.alloc_user);
+        else
+            cudaFree(p);
+        c->device_bytes -= c->allocs[k].second;
+        c->allocs.erase(c->allocs.begin() + (std::ptrdiff_t)k);
+        return;
+    }
+}
+
 void drop_graphs(lbms_ctx* c) {
     for (int k = 0; k < 2; ++k)
         if (c->graph[k]) {
@@ -179,36 +194,6 @@ lbms_status compute_props(lbms_ctx* c, const lbms_species* sp, const lbms_diffus
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) g.D_lat[i][j] = g.D_eff[i][j] * c0.dt / (c0.dx * c0.dx);
     return LBMS_OK;
-}
-
-// Neighbour rows of one case: row i holds, for k = 1..Q-1, the fluid index of
-// the source x - e_k (in the batch's index space) or an NB_* code.
-template <class Lat>
-void build_neighbours(const CaseHost& cs, const std::vector<int>& index_of, std::vector<int>& nbr) {
-    constexpr int NW = nb_width<Lat>();
-    for (int li = 0; li < cs.nf; ++li) {
-        const int64_t cell = cs.fluid_cell[li];
-        const int x = (int)(cell % cs.nx);
-        const int y = (int)((cell / cs.nx) % cs.ny);
-        const int z = (int)(cell / ((int64_t)cs.nx * cs.ny));
-        int* row = nbr.data() + (size_t)(cs.base + li) * NW;
-        for (int k = 1; k < Lat::Q; ++k) {
-            int sx = x - Lat::e(k, 0);
-            const int sy = ((y - Lat::e(k, 1)) % cs.ny + cs.ny) % cs.ny;
-            const int sz = ((z - Lat::e(k, 2)) % cs.nz + cs.nz) % cs.nz;
-            int code;
-            if (!cs.periodic_x && sx < 0) {
-                code = NB_INLET;
-            } else if (!cs.periodic_x && sx >= cs.nx) {
-                code = NB_OUTLET;
-            } else {
-                sx = (sx % cs.nx + cs.nx) % cs.nx;
-                const int j = index_of[((int64_t)sz * cs.ny + sy) * cs.nx + sx];
-                code = j >= 0 ? cs.base + j : NB_SOLID;
-            }
-            row[k - 1] = code;
-        }
-    }
 }
 
 lbms_status validate_bc(lbms_ctx* c, const double* x, double I) {
@@ -820,43 +805,51 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
     for (int v = 0; v < kStepVariants; ++v) ok = ok && L.b.blk_case[v];
     if (!ok) return bail(fail(c, LBMS_ENOMEM, "device allocation of %zu bytes failed", 2 * fbytes + 2 * xbytes + sbytes));
 
-    std::vector<int> nbr((size_t)nbw * L.S, NB_SOLID);
-    for (int k = 0; k < n_cases; ++k) {
-        if (dim == 2)
-            build_neighbours<D2Q9>(c->cases[k], index_of[k], nbr);
-        else
-            build_neighbours<D3Q19>(c->cases[k], index_of[k], nbr);
-    }
-    // the 16-bit offset table; links whose offset does not fit (periodic
-    // wraps) are marked NB16_FAR and read the 32-bit table.  Built when such
-    // links are rare (at most 1 in 16).
+    // Neighbour tables, built on the device from each case's dense
+    // fluid-index map.  The 16-bit offset table is kept when the links
+    // whose offsets do not fit (periodic wraps) are rare, at most 1 in 16;
+    // those are marked NB16_FAR and read the 32-bit table.
     const int nbw16 = dim == 2 ? nb16_width<D2Q9>() : nb16_width<D3Q19>();
-    std::vector<int16_t> nbr16;
     {
-        int64_t far = 0, links = 0;
-        for (int64_t i = 0; i < L.ncells; ++i)
-            for (int k = 0; k < c->Q - 1; ++k) {
-                const int v = nbr[(size_t)i * nbw + k];
-                if (v >= 0) {
-                    ++links;
-                    if (v - i < NB16_MIN_OFFSET || v - i > NB16_MAX_OFFSET) ++far;
-                }
-            }
-        if (far * 16 <= links) {
-            nbr16.assign((size_t)nbw16 * L.S, (int16_t)NB16_SOLID);
-            for (int64_t i = 0; i < L.ncells; ++i)
-                for (int k = 0; k < c->Q - 1; ++k) {
-                    const int v = nbr[(size_t)i * nbw + k];
-                    int code;
-                    if (v >= 0)
-                        code = (v - i < NB16_MIN_OFFSET || v - i > NB16_MAX_OFFSET) ? NB16_FAR : (int)(v - i);
-                    else
-                        code = v == NB_SOLID ? NB16_SOLID : (v == NB_INLET ? NB16_INLET : NB16_OUTLET);
-                    nbr16[(size_t)i * nbw16 + k] = (int16_t)code;
-                }
-            L.b.nbr16 = static_cast<int16_t*>(dev_alloc(c, nbr16.size() * sizeof(int16_t)));
-            if (!L.b.nbr16) return bail(fail(c, LBMS_ENOMEM, "device allocation of the 16-bit neighbour table failed"));
+        int64_t max_n = 1, max_nf = 1;
+        for (const auto& cs : c->cases) {
+            max_n = std::max<int64_t>(max_n, cs.N);
+            max_nf = std::max<int64_t>(max_nf, cs.nf);
         }
+        int16_t* nb16 = static_cast<int16_t*>(dev_alloc(c, (size_t)nbw16 * L.S * sizeof(int16_t)));
+        int* d_index = static_cast<int*>(dev_alloc(c, (size_t)max_n * sizeof(int)));
+        int64_t* d_cells = static_cast<int64_t*>(dev_alloc(c, (size_t)max_nf * sizeof(int64_t)));
+        unsigned long long* d_counts = static_cast<unsigned long long*>(dev_alloc(c, 2 * sizeof(unsigned long long)));
+        if (!d_index || !d_cells || !d_counts)
+            return bail(fail(c, LBMS_ENOMEM, "device allocation for the neighbour tables failed"));
+        e = cudaMemsetAsync(L.b.nbr, 0xFF, (size_t)nbw * L.S * sizeof(int), c->stream);   // NB_SOLID
+        if (e == cudaSuccess && nb16) e = launch_fill16(nb16, (int64_t)nbw16 * L.S, (int16_t)NB16_SOLID, c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_counts, 0, 2 * sizeof(unsigned long long), c->stream);
+        for (int k = 0; k < n_cases && e == cudaSuccess; ++k) {
+            const CaseHost& cs = c->cases[k];
+            e = cudaMemcpyAsync(d_index, index_of[k].data(), (size_t)cs.N * sizeof(int), cudaMemcpyHostToDevice,
+                                c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_cells, cs.fluid_cell.data(), (size_t)cs.nf * sizeof(int64_t),
+                                    cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = launch_build_neighbours(dim, d_cells, d_index, cs.nf, cs.base, cs.nx, cs.ny, cs.nz, cs.periodic_x,
+                                            L.b.nbr, nb16, d_counts, c->stream);
+            // the host maps are reused by the next case's copies: wait for this one
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            c->h2d += (size_t)cs.N * sizeof(int) + (size_t)cs.nf * sizeof(int64_t);
+        }
+        unsigned long long counts[2] = {0, 0};
+        if (e == cudaSuccess)
+            e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return bail(cuda_fail(c, e, "building the neighbour tables"));
+        dev_free(c, d_index);
+        dev_free(c, d_cells);
+        dev_free(c, d_counts);
+        if (nb16 && counts[1] * 16 <= counts[0])
+            L.b.nbr16 = nb16;
+        else if (nb16)
+            dev_free(c, nb16);
     }
     std::vector<int> rows;
     rows.reserve(3 * rows_x0.size());
@@ -868,8 +861,6 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         if (e == cudaSuccess && n) e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, c->stream);
         c->h2d += n;
     };
-    up(L.b.nbr, nbr.data(), nbr.size() * sizeof(int));
-    if (L.b.nbr16) up(L.b.nbr16, nbr16.data(), nbr16.size() * sizeof(int16_t));
     up(L.b.rows, rows.data(), rows.size() * sizeof(int));
     up(L.b.case_rows, case_rows.data(), case_rows.size() * sizeof(int2));
     up(L.b.segs, segs.data(), segs.size() * sizeof(int2));

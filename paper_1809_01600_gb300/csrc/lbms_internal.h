@@ -91,6 +91,15 @@ cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st);
 cudaError_t launch_case_extrap_norms(const Launch& L, cudaStream_t st);
 cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st);
 
+// Neighbour tables of one case built on the device from its dense
+// fluid-index map (index_of[cell] = index in the case or -1) and its fluid
+// cell list; nbr16 may be null.  counts[0..1] accumulate the fluid links and
+// the links that do not fit the 16-bit table.
+cudaError_t launch_build_neighbours(int dim, const int64_t* fluid_cell, const int* index_of, int nf, int base, int nx,
+                                    int ny, int nz, int periodic_x, int* nbr, int16_t* nbr16,
+                                    unsigned long long* counts, cudaStream_t st);
+cudaError_t launch_fill16(int16_t* p, int64_t n, int16_t v, cudaStream_t st);
+
 // Read-only view of one case of a handle (for the warm-start network).
 struct CaseView {
     int nx, ny, nz;
