@@ -67,9 +67,9 @@ def parse():
     ap.add_argument("--sweep-3d", type=int, default=8, help="3-D microstructures of the sweep")
     ap.add_argument("--sweep-scale", type=float, default=1.0, help="size factor of the sweep grids")
     ap.add_argument("--sweep-points", type=int, default=8, help="operating points per microstructure")
-    ap.add_argument("--ws-train", type=int, default=64, help="warm start: training anodes")
+    ap.add_argument("--ws-train", type=int, default=128, help="warm start: training anodes")
     ap.add_argument("--ws-test", type=int, default=16, help="warm start: held-out anodes")
-    ap.add_argument("--ws-iters", type=int, default=4000, help="warm start: Adam steps")
+    ap.add_argument("--ws-iters", type=int, default=6000, help="warm start: Adam steps")
     ap.add_argument("--ws-lr", type=float, default=1e-3, help="warm start: peak learning rate")
     return ap.parse_args()
 
