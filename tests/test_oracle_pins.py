@@ -128,14 +128,19 @@ def _run_1d(nx, L, current, x_in=(0.5, 0.1, 0.4), gas=None, tol=1e-13):
 
 def test_ternary_1d_closed_form_second_order():
     """Eqs. 19, 24, 25, 28, 32-36, 39: the homogeneous 1-D anode converges to
-    the ternary Maxwell-Stefan profile with Stefan flux at second order."""
-    errs, sums = [], []
+    the ternary Maxwell-Stefan profile with Stefan flux at second order; the
+    component velocities of Eq. 20 (from the fluxes of Eqs. 31-34) approach
+    u_i = N_i / (C_t X_i) with the outlet fluxes of Eq. 39 (N_Ar = 0)."""
+    errs, sums, uerr = [], [], []
     for nx in (9, 17, 33):
         o, Xc = _run_1d(nx, 1e-2, 1.0)
         X = o.X[:, 0, 0, :]
         k = (nx - 1) // 8
         errs.append(np.abs(X - Xc)[:, ::k].max())
         sums.append(np.abs(X.sum(axis=0) - 1.0).max())
+        u = o.fields()[1][:, 0, 0, 0, 1:-1]             # x components, interior nodes
+        want = o.sc.N_out[:2, None] / (o.sc.C_t * X[:2, 1:-1])
+        uerr.append(max(np.abs(u[:2] / want - 1.0).max(), np.abs(u[2]).max() / np.abs(u[0]).max()))
         # inert species: zero net flux through every plane (Eq. 39, nu_3 = 0)
         F = o.plane_flux()
         assert np.abs(F[2]).max() < 1e-9 * abs(o.sc.q_lat[0])
@@ -144,6 +149,7 @@ def test_ternary_1d_closed_form_second_order():
     assert errs[-1] < 1e-6
     assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5
     assert sums[0] / sums[1] > 3.5 and sums[1] / sums[2] > 3.5
+    assert uerr[-1] < 2e-4 and uerr[0] / uerr[1] > 1.7 and uerr[1] / uerr[2] > 1.7
 
 
 def test_overpotential_matches_closed_form_and_table2_trend():
