@@ -284,9 +284,12 @@ lbms_status lbms_synchronize(lbms_ctx *ctx);
  *                work and does not synchronise.
  * Scratch: a fixed 40 KiB device array (512 blocks x 10 partial sums) plus a
  * counter, held by every GPU that loads this library until the process
- * exits; the grid is capped at 512 blocks, so any n in range fits.  The first
- * call on a device looks up the scratch address (once per device, with that
- * device current): make that first call before any stream capture.  All calls
+ * exits; the grid is capped at 512 blocks and the kernel walks the cells with
+ * a 64-bit index, so any n in range fits.  The first call on a device looks
+ * up the scratch address (once per device, with that device current) and
+ * keeps it for the life of the process: make that first call before any
+ * stream capture, and do not use this entry point after cudaDeviceReset on
+ * that device (the module, and with it the scratch, may move).  All calls
  * share the scratch, so calls that overlap on the GPU (other streams, other
  * threads) race; serialise them.  Nothing is allocated or freed.
  * LBMS_EINVAL on NULL pointers or n out of range, LBMS_ECUDA on a CUDA error. */

@@ -764,31 +764,6 @@ __device__ __forceinline__ void reduce_to_out(double (&acc)[NV], double* __restr
     if (threadIdx.x == 0) *counter = 0u;
 }
 
-// Residual sums over fluid cells in FP64: out[0..2] = sum (X - snap)^2,
-// out[3..5] = sum X^2, out[6..8] = sum X, out[9] = count of non-finite X.
-// When update != 0 the snapshot takes X.  Grid-stride over a persistent grid.
-template <typename XS>
-__global__ void __launch_bounds__(256) residual_kernel(const XS* __restrict__ X, double* __restrict__ snap,
-                                                       int64_t S, int nf, int update, double* __restrict__ partials,
-                                                       unsigned int* __restrict__ counter, double* __restrict__ out) {
-    double acc[10];
-#pragma unroll
-    for (int v = 0; v < 10; ++v) acc[v] = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nf; i += gridDim.x * blockDim.x) {
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const double x = Xv<XS>::own(X, S, s, i).to_double();
-            const double d = x - snap[s * S + i];
-            acc[s] += d * d;
-            acc[3 + s] += x * x;
-            acc[6 + s] += x;
-            if (!isfinite(x)) acc[9] += 1.0;
-            if (update) snap[s * S + i] = x;
-        }
-    }
-    reduce_to_out<10>(acc, partials, counter, out);
-}
-
 // -------------------------------------------------------------------------
 // Per-case FP64 reductions of a batch, deterministic: a first kernel writes
 // one partial per segment (a run of at most kSegCells cells of one case),

@@ -122,3 +122,16 @@ def test_calls_on_null_handle_fail_cleanly():
     assert lib.lbms_residual(None, 1, C.byref(r)) == L.LBMS_ESTATE
     assert lib.lbms_set_bc(None, None, 0.0) == L.LBMS_ESTATE
     lib.lbms_destroy(None)
+
+
+def test_noalloc_size_bounds_checked_on_the_host():
+    """lbms_residual_sums_noalloc refuses n outside [1, INT32_MAX] before any
+    CUDA call (the pointers below are never dereferenced): its kernel walks
+    the cells with a 64-bit index, so every accepted n is safe."""
+    lib = L.load()
+    fake = C.c_void_p(0x1000)
+    for n in (0, -1, 2 ** 31, 2 ** 40):
+        assert lib.lbms_residual_sums_noalloc(fake, fake, n, 0, fake, None) == L.LBMS_EINVAL
+    assert lib.lbms_residual_sums_noalloc(None, fake, 5, 0, fake, None) == L.LBMS_EINVAL
+    assert lib.lbms_residual_sums_noalloc(fake, None, 5, 0, fake, None) == L.LBMS_EINVAL
+    assert lib.lbms_residual_sums_noalloc(fake, fake, 5, 0, None, None) == L.LBMS_EINVAL
