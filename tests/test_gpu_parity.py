@@ -149,8 +149,10 @@ def test_pulse_variance_on_gpu(lbms):
 def test_graph_replay_equals_single_steps(lbms):
     case = cases.porous((20, 30), radius=3, porosity=0.55, seed=25, current_A_cm2=1.0)
     X0 = smooth_field(case.solid.shape, 8)
-    a = lbms.Solver.from_case(case, precision="fp32")
-    b = lbms.Solver.from_case(case, precision="fp32")
+    # one forced kernel variant for both handles: the autotuner times each
+    # handle separately and may pick variants that round differently
+    a = lbms.Solver.from_case(case, precision="fp32", step_variant=7)
+    b = lbms.Solver.from_case(case, precision="fp32", step_variant=7)
     for s in (a, b):
         s.set_bc(case.x_in, case.current_A_cm2)
         s.set_fields(X0)
