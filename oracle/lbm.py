@@ -23,9 +23,14 @@ One time step t (all quantities in lattice units, c_s^2 = 1/3):
    Eq. 36 rule f_a = (w_a + w_abar) X_out - f_abar.
 2. Moments: X_i = sum_a f_a (the zeroth moment of Eq. 29's distribution).
 3. Gradient of the stored field of the previous step (Eq. 35, read as a
-   central difference on every axis): (X(x+e) - X(x-e))/2; a solid
-   neighbour takes the centre value (mirror about the half-way wall); at the
-   x = 0 / x = nx-1 nodes the one-sided difference is used.
+   central difference on every axis; a fused one-pass step can only see its
+   neighbours' X of the step before).  lag=False follows the order of
+   Section 3.2 instead: the gradient of the moments of step 2 of this very
+   step, after every cell has taken them.  Either way the steady state is
+   the same (X then no longer changes from step to step).  The stencil:
+   (X(x+e) - X(x-e))/2; a solid neighbour takes the centre value (mirror
+   about the half-way wall); at the x = 0 / x = nx-1 nodes the one-sided
+   difference is used.
    grad_stencil="forward" takes Eq. 35 literally: X(x+1) - X(x) along x
    only (backward at x = nx-1), zero along y and z.
 4. Maxwell-Stefan coupling with species 3 (Ar) as the reference n:
@@ -33,6 +38,7 @@ One time step t (all quantities in lattice units, c_s^2 = 1/3):
    Gamma = I, Eq. 30 ideal gas); J_3 from the n-th row of Eq. 19 given
    J_1, J_2 (not from the closure of Eq. 21, which leaves sum X - 1 without
    a restoring term); N = J (Eq. 20, u_M = 0, Section 3.1).
+   closure="eq21" takes Section 3.2 literally instead: J_3 = -J_1 - J_2.
 5. Effective diffusivity, Eq. 24, with the paper's rule that each flux
    points as its stoichiometric coefficient says (Section 3.1) and its
    observation that the fluxes across the thin anode stay at their A/E values
@@ -71,7 +77,7 @@ V_MAX = 0.1           # bound on |v_i| (lattice units)
 
 class Oracle:
     def __init__(self, case, tau_min=1.0, tau_max=5.0, coupling="ms", dt=None,
-                 grad_stencil="central", outlet_bc="flux"):
+                 grad_stencil="central", outlet_bc="flux", lag=True, closure="row_n"):
         self.case = case
         self.solid = np.asarray(case.solid, dtype=bool)
         self.fluid = ~self.solid
@@ -90,8 +96,12 @@ class Oracle:
         self.coupling = coupling
         if grad_stencil not in ("central", "forward") or outlet_bc not in ("flux", "extrapolated"):
             raise ValueError("grad_stencil: central | forward; outlet_bc: flux | extrapolated")
+        if closure not in ("row_n", "eq21"):
+            raise ValueError("closure: row_n | eq21")
         self.grad_stencil = grad_stencil
         self.outlet_bc = outlet_bc
+        self.lag = bool(lag)
+        self.closure = closure
         self.t = 0
         self.init()
 
@@ -202,11 +212,15 @@ class Oracle:
         g1, g2, g3 = G[0], G[1], G[2]
         j1 = -(B22 * g1 - B12 * g2) * inv_det
         j2 = -(B11 * g2 - B21 * g1) * inv_det
-        # species n from its own row of Eq. 19 given N_1, N_2
-        d3 = X1 / D13 + X2 / D23
-        with np.errstate(divide="ignore", invalid="ignore"):
-            inv_d3 = np.where(d3 > 0, 1.0 / np.where(d3 > 0, d3, 1.0), 0.0)
-        j3 = (-g3 + X3[None] * (j1 / D13 + j2 / D23)) * inv_d3
+        if self.closure == "eq21":
+            # Section 3.2 literally: N_n = -(N_1 + N_2) (Eq. 21 with u_M = 0)
+            j3 = -j1 - j2
+        else:
+            # species n from its own row of Eq. 19 given N_1, N_2
+            d3 = X1 / D13 + X2 / D23
+            with np.errstate(divide="ignore", invalid="ignore"):
+                inv_d3 = np.where(d3 > 0, 1.0 / np.where(d3 > 0, d3, 1.0), 0.0)
+            j3 = (-g3 + X3[None] * (j1 / D13 + j2 / D23)) * inv_d3
         J = np.stack([j1, j2, j3])
 
         nu = self.sc.stoich
@@ -243,7 +257,7 @@ class Oracle:
             P = self._stream()
             X = P.sum(axis=1)
             X[:, self.solid] = 0.0
-            G = self._gradient(self.Xprev)
+            G = self._gradient(self.Xprev if self.lag else X)
             tau, v, u = self._coupling(X, G)
             Anew = np.empty_like(P)
             for a in range(self.Q):

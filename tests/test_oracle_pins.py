@@ -10,6 +10,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
+import closed_forms as cf
 from closed_forms import binary_linear, nernst_overpotential, pulse_variance, ternary_1d
 from oracle import Oracle, d2q9, d3q19, effective_binary, fuller_binary, knudsen
 from oracle.gas import R_GAS, total_concentration
@@ -101,6 +102,160 @@ def test_knudsen_and_effective_invariants():
     assert total_concentration(1000.0, 1e5) == pytest.approx(1e5 / (R_GAS * 1000.0), rel=1e-15)
 
 
+def test_gas_data_against_independent_closed_form():
+    """Eqs. 39-42 and C_t = p/RT of the oracle against closed_forms, which
+    computes them with its own constants and unit conversions: a wrong
+    Fuller constant, exponent or pressure unit, Knudsen factor, Eq. 41
+    weighting or Eq. 39 scale (n, F, the A/cm^2 factor) fails here."""
+    for T, p, dp, phi in ((1073.0, 101325.0, 1e-6, 1.0), (1023.15, 1.013e5, 2.6e-6, 0.46 / 4.5),
+                          (900.0, 2.0e5, 0.0, 0.3)):
+        gas = cases.Gas(T=T, p=p, pore_diameter=dp, eps_over_tau=phi)
+        c = cases.open_channel(11, 1, current_A_cm2=0.7, length_x=2e-3, gas=gas)
+        sc = Oracle(c).sc
+        D, Ct = cf.gas_point(T, p, dp, phi)
+        assert np.allclose(sc.D_eff, D, rtol=1e-13, atol=0)
+        assert sc.C_t == pytest.approx(Ct, rel=1e-14)
+        assert np.allclose(sc.N_out, cf.outlet_flux(0.7), rtol=1e-14, atol=0)
+        assert sc.dx == pytest.approx(2e-3 / 10, rel=1e-15)
+        assert np.allclose(sc.q_lat, cf.outlet_flux(0.7) * sc.dt / (Ct * sc.dx), rtol=1e-13, atol=0)
+
+
+def test_hand_derived_gas_data_and_1d_anode():
+    """Values worked out by hand from Table 1 and Eqs. 19 and 39-43 at
+    1073 K, 1 atm, d_p = 1 um, eps/tau = 1, X_in = (0.5, 0.1, 0.4),
+    L = 2 mm (they are not printed in the paper), to the digits given:
+    D_eff = 4.326e-4 (H2-H2O), 3.765e-4 (H2-Ar), 1.607e-4 (H2O-Ar) m^2/s,
+    C_t = 11.357 mol/m^3; at 0.5 A/cm^2, N = 2.591e-2 mol/(m^2 s), X_out =
+    (0.488829, 0.117626, 0.393545), eta = 8.550 mV; at 1.0 A/cm^2, X_out =
+    (0.477668, 0.135138, 0.387193), eta = 16.034 mV.  Checked against the
+    closed forms and against the oracle's 1-D steady state (nx = 33, second
+    order in dx, so a few 1e-6 from the continuum)."""
+    D, Ct = cf.gas_point(1073.0, 101325.0, 1e-6, 1.0)
+    assert D[0, 1] == pytest.approx(4.326e-4, abs=0.0005e-4)
+    assert D[0, 2] == pytest.approx(3.765e-4, abs=0.0005e-4)
+    assert D[1, 2] == pytest.approx(1.607e-4, abs=0.0005e-4)
+    assert Ct == pytest.approx(11.357, abs=0.0005)
+    assert cf.outlet_flux(0.5)[0] == pytest.approx(2.591e-2, abs=0.0005e-2)
+    want = {0.5: ((0.488829, 0.117626, 0.393545), 8.550e-3), 1.0: ((0.477668, 0.135138, 0.387193), 16.034e-3)}
+    for I, (xo, eta) in want.items():
+        X = cf.anode_1d(np.array([2e-3]), (0.5, 0.1, 0.4), I, 1073.0, 101325.0, 1e-6, 1.0)[:, -1]
+        assert np.allclose(X, xo, atol=0.5e-6)
+        assert nernst_overpotential(1073.0, (0.5, 0.1, 0.4), X) == pytest.approx(eta, abs=0.0005e-3)
+        o, _ = _run_1d(33, 2e-3, I, tol=1e-13)
+        assert np.allclose(o.outlet_mean(), xo, atol=5e-6)
+        assert o.overpotential() == pytest.approx(eta, rel=2e-4)
+
+
+def test_table2_closed_form_eta_minus_eta0():
+    """The homogenised Table 2 anode (1023.15 K, 1.013e5 Pa, eps/tau =
+    0.46/4.5, d_p = 2.6 um, L = 2 mm, H2:H2O = 4:1 diluted by Ar; eta_0 at
+    X_H2 = 0.8): eta - eta_0 (V) worked out by hand from Eqs. 19 and 39-43,
+    to four decimals.  Rows 0.3, 0.7, 1.0 A/cm^2 (Figs. 2-4); columns
+    X_H2,in = 0.6, 0.4, 0.3, 0.2."""
+    table = {0.3: (0.0073, 0.0197, 0.0302, 0.0475),
+             0.7: (0.0135, 0.0348, 0.0522, 0.0827),
+             1.0: (0.0170, 0.0434, 0.0659, 0.1124)}
+    g = cases.PAPER_TABLE2
+
+    def eta(I, xh):
+        x_in = (xh, xh / 4.0, 1.0 - 1.25 * xh)
+        X = cf.anode_1d(np.array([2e-3]), x_in, I, g.T, g.p, g.pore_diameter, g.eps_over_tau)[:, -1]
+        return nernst_overpotential(g.T, x_in, X)
+
+    for I, row in table.items():
+        e0 = eta(I, 0.8)
+        for xh, v in zip((0.6, 0.4, 0.3, 0.2), row):
+            assert eta(I, xh) - e0 == pytest.approx(v, abs=0.5e-4), (I, xh)
+
+
+def test_eq24_tau_at_unequal_diffusivities():
+    """Eq. 24 evaluated with the fluxes of the 1-D steady state, N_1 = -N_2 =
+    I/2F and N_3 = 0 (Eq. 39, Section 3.1), at strongly unequal D_ij:
+    1/D_1 = (X_1 + X_2)/D_12 + X_3/D_13 and 1/D_2 = (X_1 + X_2)/D_12 +
+    X_3/D_23, so tau_i = D_i/c_s^2 + 1/2 (Eq. 25) in lattice units.  For Ar
+    (N_3 = 0) Eq. 24 is singular and the mixture value
+    (X_1 + X_2)/(X_1/D_13 + X_2/D_23) is taken.  An index or sign slip in
+    the oracle's Eq. 24 coefficients moves tau_1 or tau_2 off these values."""
+    Db = np.array([[0.0, 6e-4, 3e-4], [6e-4, 0.0, 1.5e-4], [3e-4, 1.5e-4, 0.0]])
+    gas = cases.Gas(D_binary=Db, pore_diameter=0.0, eps_over_tau=1.0)
+    c = cases.open_channel(17, 1, current_A_cm2=1.5, length_x=4e-3, gas=gas)
+    o = Oracle(c)
+    _, Ct = cf.gas_point(gas.T, gas.p, 0.0, 1.0)
+    N = cf.outlet_flux(1.5)
+    x = np.arange(17) * (4e-3 / 16)
+    o.init(ternary_1d(x, c.x_in, N[0], Ct, Db[0, 1], Db[0, 2], Db[1, 2])[:, None, None, :])
+    n, r = o.run_to_residual(1e-13, 400000, 100)
+    assert r <= 1e-13
+    X1, X2, X3 = (o.X[i, 0, 0] for i in range(3))
+    lat = o.sc.dt / o.sc.dx ** 2           # m^2/s -> lattice units
+    D = {}
+    for i, (k, l) in ((0, (1, 2)), (1, (0, 2))):
+        # 1/D_i = sum_j X_j / D_ij - X_i N_j / (D_ij N_i), j != i
+        inv = sum(o.X[j, 0, 0] / Db[i, j] - o.X[i, 0, 0] * N[j] / (Db[i, j] * N[i]) for j in (k, l))
+        D[i] = 1.0 / inv
+    assert np.allclose(1.0 / D[0], (X1 + X2) / Db[0, 1] + X3 / Db[0, 2], rtol=1e-14)
+    D[2] = (X1 + X2) / (X1 / Db[0, 2] + X2 / Db[1, 2])
+    for i in range(3):
+        tau = 3.0 * D[i] * lat + 0.5
+        assert np.all((tau > 1.0) & (tau < 5.0)), i        # the clamp of Eq. 25 is inactive
+        assert np.allclose(o.tau[i, 0, 0], tau, rtol=1e-12, atol=0), i
+    assert np.abs(o.tau[0] - o.tau[1]).max() > 0.1           # the D_ij really differ
+
+
+@pytest.mark.parametrize("kind", ["1d", "porous"])
+def test_lagged_gradient_reaches_the_paper_order_steady_state(kind):
+    """Section 3.2 computes Eq. 35 on the moments of the current step; the
+    fused kernel (and the default oracle) can only use the previous step's
+    field.  At steady state X no longer changes, so both orders must reach
+    the same state."""
+    if kind == "1d":
+        c = cases.open_channel(17, 1, current_A_cm2=1.0, length_x=1e-2)
+    else:
+        c = cases.porous((12, 20), radius=2, porosity=0.6, seed=7, current_A_cm2=1.0)
+    res = []
+    for lag in (True, False):
+        o = Oracle(c, lag=lag)
+        n, r = o.run_to_residual(1e-13, 400000, 100)
+        assert r <= 1e-13
+        res.append(o.X.copy())
+    assert np.abs(res[0] - res[1]).max() < 1e-10
+    # and the two orders do differ on the way there
+    a, b = Oracle(c, lag=True), Oracle(c, lag=False)
+    a.step(50)
+    b.step(50)
+    assert np.abs(a.X - b.X).max() > 1e-8
+
+
+@pytest.mark.slow
+def test_eq21_closure_drifts():
+    """Section 3.2 takes Ar's flux from Eq. 21, N_3 = -(N_1 + N_2).  With that
+    closure nothing restores sum_i X_i = 1: on the 1-D anode the residual
+    stalls near 1e-8, sum X - 1 keeps growing and Ar carries a net flux.
+    With Ar's own row of Eq. 19 (the reading used) the same run converges
+    to rounding, sum X - 1 settles at its O(dx^2) value and Ar's net flux
+    vanishes."""
+    out = {}
+    for closure in ("row_n", "eq21"):
+        c = cases.open_channel(17, 1, current_A_cm2=1.0, length_x=1e-2)
+        o = Oracle(c, closure=closure)
+        o.step(20000)
+        o.residual(1)
+        o.step(5000)
+        r1 = o.residual(5000)
+        s1 = np.abs(o.X.sum(axis=0) - 1.0).max()
+        o.step(5000)
+        r2 = o.residual(5000)
+        s2 = np.abs(o.X.sum(axis=0) - 1.0).max()
+        far = np.abs(o.plane_flux()[2]).max() / abs(o.sc.q_lat[0])
+        out[closure] = (r1, r2, s1, s2, far)
+    r1, r2, s1, s2, far = out["row_n"]
+    assert r2 < 1e-13 and abs(s2 - s1) < 1e-12 and s2 < 1e-5 and far < 1e-9
+    r1, r2, s1, s2, far = out["eq21"]
+    assert r2 > 5e-9 and r2 > 0.5 * r1         # stalled
+    assert s2 > s1 + 1e-5                      # sum X - 1 still growing
+    assert far > 1e-5
+
+
 # ------------------------------------------------------------- P4: I = 0
 def test_zero_current_keeps_inlet_state():
     c = cases.porous((16, 24), radius=3, porosity=0.6, seed=5, current_A_cm2=0.0)
@@ -113,13 +268,20 @@ def test_zero_current_keeps_inlet_state():
 
 
 # ---------------------------------------- P1: 1-D ternary closed form
-def _run_1d(nx, L, current, x_in=(0.5, 0.1, 0.4), gas=None, tol=1e-13):
+def _closed_form_1d(c):
+    """The closed-form profile at the nodes x_j = j L / (nx - 1) of a 1-D
+    case, with gas data computed by closed_forms (not by the oracle)."""
+    g = c.gas
+    nx = c.solid.shape[2]
+    x = np.arange(nx) * (c.length_x / (nx - 1))
+    return cf.anode_1d(x, c.x_in, c.current_A_cm2, g.T, g.p, g.pore_diameter, g.eps_over_tau)
+
+
+def _run_1d(nx, L, current, x_in=(0.5, 0.1, 0.4), gas=None, tol=1e-13, **okw):
     c = cases.open_channel(nx, 1, current_A_cm2=current, length_x=L, x_in=x_in,
                            gas=gas or cases.Gas())
-    o = Oracle(c)
-    sc = o.sc
-    x = np.arange(nx) * sc.dx
-    Xc = ternary_1d(x, x_in, sc.N_out[0], sc.C_t, sc.D_eff[0, 1], sc.D_eff[0, 2], sc.D_eff[1, 2])
+    o = Oracle(c, **okw)
+    Xc = _closed_form_1d(c)
     o.init(Xc[:, None, None, :])
     n, r = o.run_to_residual(tol, 400000, 100)
     assert r <= tol
@@ -306,8 +468,7 @@ def _order_1d(grad_stencil, outlet_bc):
         c = cases.open_channel(nx, 1, current_A_cm2=1.0, length_x=2e-3)
         o = Oracle(c, grad_stencil=grad_stencil, outlet_bc=outlet_bc)
         sc = o.sc
-        Xc = ternary_1d(np.arange(nx) * sc.dx, c.x_in, sc.N_out[0], sc.C_t,
-                        sc.D_eff[0, 1], sc.D_eff[0, 2], sc.D_eff[1, 2])
+        Xc = _closed_form_1d(c)
         o.init(Xc[:, None, None, :])
         n, r = o.run_to_residual(1e-12, 400000, 100)
         assert r <= 1e-12
