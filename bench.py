@@ -100,11 +100,15 @@ def make_case(name):
 
 def bytes_per_cell(dim, precision):
     """Algorithmic bytes per fluid-cell update (3 species): one read and one
-    write of every stored population (non-equilibrium part, 8/4/2 bytes) and
-    of the mole fraction (FP64, or an 8-byte double-float pair)."""
+    write of the Q populations of each species and of its mole fraction, at
+    the method's precision: populations 8/4/2 bytes, X 8 bytes in FP64 and 4
+    in the single-precision forms (160 B per species-update for D3Q19 FP32,
+    84 B with 16-bit populations).  The solver's FP32 forms carry X as a
+    double-float pair (8 bytes); the second word is its own extra precision,
+    not work of the method, and is not counted."""
     q = 9 if dim == 2 else 19
     ps = {"fp64": 8, "fp32": 4, "fp16": 2}[precision]
-    xs = 8
+    xs = 8 if precision == "fp64" else 4
     return 3 * (2 * q * ps + 2 * xs)
 
 
@@ -181,7 +185,8 @@ def kernel_source_sha():
 
 def variant_key(info):
     """Step-kernel variant as written in profiles/traffic.txt: cells per block
-    x resident blocks, threads per cell, neighbour-index bits."""
+    x resident blocks, threads per cell, neighbour lookup (32 / 16 bits per
+    link, or 1: the per-row fluid bitmasks)."""
     return f"{info.tile_cells}x{info.tile_min_blocks}/t{info.threads_per_cell}/nb{info.neighbour_bits}"
 
 

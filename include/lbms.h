@@ -100,9 +100,13 @@ typedef struct {
  *             0 = off [0]
  *  step_variant  0: the autotuner picks the step kernel's tile, thread
  *             mapping (a thread per cell and species, or per cell) and
- *             neighbour table by timing; k in 1..8 forces variant k - 1 (for
- *             tests), an unavailable one (16-bit table not built) is an
- *             error [0]
+ *             neighbour lookup by timing; k in 1..10 forces variant k - 1
+ *             (for tests).  Variants 0-5 and 6-7 read a table of 32-bit
+ *             fluid indices (or 16-bit offsets, 3-5) per cell and link;
+ *             8-9 decode the neighbours from per-row fluid bitmasks and a
+ *             4-byte coordinate per cell (built when no case is periodic in
+ *             x and nx <= 2048, ny <= 1024, nz <= 2048).  An unavailable
+ *             variant is an error [0]
  *  init_mode  state a case starts from at its first set_bc:
  *             LBMS_INIT_UNIFORM: the inlet composition everywhere, f = w X_in;
  *             LBMS_INIT_PROFILE_1D: the initial state of Section 4.1, every
@@ -118,7 +122,7 @@ typedef struct {
  *             Eq. 19 over one spacing at the Eq. 39 fluxes, applied with the
  *             Eq. 36 rule (first order: the delivered flux approaches q as
  *             dx -> 0); computed by the per-cell step kernel only, so the
- *             autotuner then picks among variants 6-7 [FLUX]
+ *             autotuner then picks among the per-cell variants 6-9 [FLUX]
  *  grad_stencil  LBMS_GRAD_CENTRAL: central differences of the previous
  *             step's X on every axis (one-sided at x = 0, nx-1);
  *             LBMS_GRAD_FORWARD: Eq. 35 as printed, the forward difference
@@ -160,7 +164,7 @@ typedef struct {
     int n_cases;                /* cases in the handle (1 unless made by lbms_create_batch) */
     int tile_cells;             /* step-kernel tile picked by the autotuner: cells per block */
     int tile_min_blocks;        /*   and its register budget (resident blocks per SM) */
-    int neighbour_bits;         /*   and its neighbour table: 32-bit indices or 16-bit offsets */
+    int neighbour_bits;         /*   and its neighbour lookup: 32 (indices), 16 (offsets) or 1 (row bitmasks) */
     int threads_per_cell;       /*   and its thread mapping: 3 (one per species) or 1 */
 } lbms_info;
 /* n_cells and n_fluid sum over all cases; dx_m, dt_s, q_lat, x_in and

@@ -28,6 +28,7 @@ struct CaseHost {
     double length_x = 0.0;
     std::vector<int64_t> fluid_cell;  // dense index of each fluid cell, x-fastest order
     int base = 0, nf = 0;             // range [base, base + nf) of the kernels' index space
+    int wpr = 0, tab = 0;             // row-bitmask table: entries per row, first entry of the case
     int row_first = 0, nrows = 0;     // rows (y, z) in the concatenated row lists
     double dx = 0.0, dt = 0.0;
     double x_in[3] = {0, 0, 0};
@@ -218,6 +219,11 @@ lbms_status upload_case_bc(lbms_ctx* c, int k) {
     }
     h.base = cs.base;
     h.nf = cs.nf;
+    h.nx = cs.nx;
+    h.ny = cs.ny;
+    h.nz = cs.nz;
+    h.wpr = cs.wpr;
+    h.tab = cs.tab;
     const size_t sz = case_bc_size(c->L.precision);
     pack_case_bc(c->L.precision, h, c->case_bc.data() + k * sz);
     CK(cudaMemcpyAsync(static_cast<unsigned char*>(c->L.b.cases) + k * sz, c->case_bc.data() + k * sz, sz,
@@ -255,8 +261,13 @@ lbms_status autotune(lbms_ctx* c) {
     Launch& L = c->L;
     if (c->opt.step_variant > 0) {
         const int v = c->opt.step_variant - 1;
-        if (kVariantNb16[v] && !L.b.nbr16)
+        if (kVariantNb[v] == kNbOffset16 && !L.b.nbr16)
             return fail(c, LBMS_EINVAL, "step variant %d needs the 16-bit neighbour table, which was not built", v);
+        if (kVariantNb[v] == kNbRowMask && !L.b.rowtab)
+            return fail(c, LBMS_EINVAL,
+                        "step variant %d needs the row-bitmask tables (no box periodic in x, nx <= %d, ny <= %d, "
+                        "nz <= %d)",
+                        v, kRowMaskMaxNx, kRowMaskMaxNy, kRowMaskMaxNz);
         L.variant = v;
         c->tuned = true;
         return LBMS_OK;
@@ -268,7 +279,8 @@ lbms_status autotune(lbms_ctx* c) {
     int pick = L.outlet_extrap ? 6 : 0;
     cudaError_t e = cudaSuccess;
     for (int v = 0; v < kStepVariants && e == cudaSuccess; ++v) {
-        if (kVariantNb16[v] && !L.b.nbr16) continue;
+        if (kVariantNb[v] == kNbOffset16 && !L.b.nbr16) continue;
+        if (kVariantNb[v] == kNbRowMask && !L.b.rowtab) continue;
         if (L.outlet_extrap && !kVariantPerCell[v]) continue;   // the per-cell kernel alone has it
         e = launch_step_variant(L, v, c->stream);  // warm-up
         if (e != cudaSuccess) break;
@@ -644,7 +656,7 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         return bail(fail(c, LBMS_EINVAL, "grad_stencil must be LBMS_GRAD_CENTRAL or LBMS_GRAD_FORWARD"));
     if (c->opt.outlet_bc == LBMS_OUTLET_EXTRAPOLATED && c->opt.step_variant > 0 &&
         !kVariantPerCell[c->opt.step_variant - 1])
-        return bail(fail(c, LBMS_EINVAL, "the extrapolated outlet needs a per-cell step variant (7 or 8)"));
+        return bail(fail(c, LBMS_EINVAL, "the extrapolated outlet needs a per-cell step variant (7 to 10)"));
     if (n_cases < 1) return bail(fail(c, LBMS_EINVAL, "n_cases must be >= 1"));
     if (!geoms) return bail(fail(c, LBMS_EINVAL, "geometry is NULL"));
     if (!sp) return bail(fail(c, LBMS_EINVAL, "species is NULL"));
@@ -850,6 +862,70 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
             L.b.nbr16 = nb16;
         else if (nb16)
             dev_free(c, nb16);
+    }
+    // Row-bitmask decode (kNbRowMask variants): a coordinate word per cell
+    // and, per case, (y, z) row and 32-voxel word w, a 64-bit window of the
+    // fluid flags of voxels 32 w - 16 .. 32 w + 47 and the fluid index of the
+    // first fluid voxel at or after 32 w - 16.  Built on the host from the
+    // fluid-index maps; not built when a case is periodic in x or too large
+    // for the coordinate word.
+    {
+        bool ok_rm = true;
+        int64_t entries = 0;
+        for (const auto& cs : c->cases) {
+            ok_rm = ok_rm && !cs.periodic_x && cs.nx <= kRowMaskMaxNx && cs.ny <= kRowMaskMaxNy &&
+                    cs.nz <= kRowMaskMaxNz;
+            entries += (int64_t)cs.ny * cs.nz * ((cs.nx + 31) / 32);
+        }
+        ok_rm = ok_rm && entries < (int64_t)std::numeric_limits<int>::max();
+        if (ok_rm) {
+            std::vector<uint32_t> code((size_t)L.S, 0xFFFFFFFFu);
+            std::vector<uint4> tab((size_t)entries);
+            int64_t next_tab = 0;
+            for (int k = 0; k < n_cases; ++k) {
+                CaseHost& cs = c->cases[k];
+                cs.wpr = (cs.nx + 31) / 32;
+                cs.tab = (int)next_tab;
+                next_tab += (int64_t)cs.ny * cs.nz * cs.wpr;
+                for (int li = 0; li < cs.nf; ++li) {
+                    const int64_t cell = cs.fluid_cell[li];
+                    const uint32_t x = (uint32_t)(cell % cs.nx);
+                    const uint32_t y = (uint32_t)((cell / cs.nx) % cs.ny);
+                    const uint32_t z = (uint32_t)(cell / ((int64_t)cs.nx * cs.ny));
+                    code[(size_t)cs.base + li] = x | (y << 11) | (z << 21);
+                }
+                std::vector<uint32_t> words((size_t)cs.wpr + 2);   // words[m + 1] = voxels 32 m .. 32 m + 31
+                int count = cs.base;                                // fluid index of the next fluid voxel
+                for (int r = 0; r < cs.ny * cs.nz; ++r) {
+                    std::fill(words.begin(), words.end(), 0u);
+                    const int* row = index_of[k].data() + (int64_t)r * cs.nx;
+                    for (int x = 0; x < cs.nx; ++x)
+                        if (row[x] >= 0) words[(size_t)(x >> 5) + 1] |= 1u << (x & 31);
+                    for (int w = 0; w < cs.wpr; ++w) {
+                        const uint64_t win = (uint64_t)(words[w] >> 16) | ((uint64_t)words[w + 1] << 16) |
+                                             ((uint64_t)(words[w + 2] & 0xFFFFu) << 48);
+                        // count = index of the first fluid voxel at or after 32 w; the
+                        // window starts 16 voxels earlier
+                        const int before = count - __builtin_popcount(words[w] >> 16);
+                        tab[(size_t)cs.tab + (size_t)r * cs.wpr + w] =
+                            make_uint4((uint32_t)win, (uint32_t)(win >> 32), (uint32_t)before, 0u);
+                        count += __builtin_popcount(words[w + 1]);
+                    }
+                }
+                if (count != cs.base + cs.nf) return bail(fail(c, LBMS_EINVAL, "case %d: row table count mismatch", k));
+            }
+            L.b.cell_code = static_cast<uint32_t*>(dev_alloc(c, (size_t)L.S * sizeof(uint32_t)));
+            L.b.rowtab = static_cast<uint4*>(dev_alloc(c, (size_t)std::max<int64_t>(entries, 1) * sizeof(uint4)));
+            if (!L.b.cell_code || !L.b.rowtab) return bail(fail(c, LBMS_ENOMEM, "row-bitmask tables"));
+            e = cudaMemcpyAsync(L.b.cell_code, code.data(), code.size() * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                c->stream);
+            if (e == cudaSuccess && entries)
+                e = cudaMemcpyAsync(L.b.rowtab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+            if (e != cudaSuccess) return bail(cuda_fail(c, e, "upload of the row-bitmask tables"));
+            c->h2d += code.size() * sizeof(uint32_t) + tab.size() * sizeof(uint4);
+        }
     }
     std::vector<int> rows;
     rows.reserve(3 * rows_x0.size());
@@ -1134,7 +1210,7 @@ lbms_status lbms_get_info(const lbms_ctx* c, lbms_info* info) {
     info->n_cases = (int)c->cases.size();
     info->tile_cells = kVariantCells[c->L.variant];
     info->tile_min_blocks = kVariantMinBlocks[c->L.variant];
-    info->neighbour_bits = kVariantNb16[c->L.variant] ? 16 : 32;
+    info->neighbour_bits = kVariantNb[c->L.variant] == kNbOffset16 ? 16 : (kVariantNb[c->L.variant] == kNbRowMask ? 1 : 32);
     info->threads_per_cell = kVariantPerCell[c->L.variant] ? 1 : 3;
     return LBMS_OK;
 }

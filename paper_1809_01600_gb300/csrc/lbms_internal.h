@@ -14,14 +14,21 @@ namespace lbms {
 constexpr int kCaseOutSlots = 16;      // doubles per case: residual sums (10) | boundary sums (6)
 
 // Step-kernel variants the autotuner chooses from: (cells per block, minimum
-// resident blocks per SM for the register budget, neighbour table of 16-bit
-// offsets instead of 32-bit indices, one thread per cell for all species
-// instead of one per (cell, species)).
-constexpr int kStepVariants = 8;
-constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64, 64, 32};
-constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4, 8, 16};
-constexpr int kVariantNb16[kStepVariants] = {0, 0, 0, 1, 1, 1, 0, 0};
-constexpr int kVariantPerCell[kStepVariants] = {0, 0, 0, 0, 0, 0, 1, 1};
+// resident blocks per SM for the register budget, how neighbours are found,
+// one thread per cell for all species instead of one per (cell, species)).
+// Neighbours: kNbIndex32 reads a row of 32-bit fluid indices per cell,
+// kNbOffset16 a row of 16-bit offsets, kNbRowMask decodes them from per-row
+// fluid bitmasks and a 4-byte coordinate per cell (no per-link table).
+enum { kNbIndex32 = 0, kNbOffset16 = 1, kNbRowMask = 2 };
+constexpr int kStepVariants = 10;
+constexpr int kVariantCells[kStepVariants] = {32, 32, 64, 32, 32, 64, 64, 32, 64, 32};
+constexpr int kVariantMinBlocks[kStepVariants] = {8, 6, 4, 8, 6, 4, 8, 16, 8, 16};
+constexpr int kVariantNb[kStepVariants] = {kNbIndex32,  kNbIndex32, kNbIndex32, kNbOffset16, kNbOffset16,
+                                           kNbOffset16, kNbIndex32, kNbIndex32, kNbRowMask,  kNbRowMask};
+constexpr int kVariantPerCell[kStepVariants] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 1};
+
+// Limits of the per-cell coordinate word of kNbRowMask (x | y << 11 | z << 21).
+constexpr int kRowMaskMaxNx = 2048, kRowMaskMaxNy = 1024, kRowMaskMaxNz = 2048;
 
 struct DevBuffers {
     void* f[2] = {nullptr, nullptr};   // non-equilibrium populations h = f* - w X, [3][Q][S]
@@ -29,6 +36,8 @@ struct DevBuffers {
     double* snap = nullptr;            // residual snapshot, [3][S]
     int* nbr = nullptr;                // [S][nb_width]
     int16_t* nbr16 = nullptr;          // [S][nb16_width] offsets, when they all fit (else null)
+    uint32_t* cell_code = nullptr;     // [S] x | y << 11 | z << 21 of each fluid cell (kNbRowMask; else null)
+    uint4* rowtab = nullptr;           // per case [rows][words]: 64-bit fluid window + index (kNbRowMask)
     int* rows = nullptr;               // [3][total rows]: x = 0, x = 1, x = nx-1 cell of each row (-1 if solid)
     int2* case_rows = nullptr;         // [cases]: first row, row count
     void* cases = nullptr;             // [cases] CaseBC<XS> (inlet values, outlet flux, range)
@@ -39,6 +48,10 @@ struct DevBuffers {
     double* partials = nullptr;        // [segments][10]
     double* extrap = nullptr;          // [3][S] X of the last extrapolation check (lazy)
     double* coef = nullptr;            // [cases] extrapolation factors
+    double* rre_ring = nullptr;        // [order + 1][3][S] X snapshots of a reduced-rank extrapolation cycle (lazy)
+    double* rre_partials = nullptr;    // [segments][order (order + 1) / 2] Gram partials (lazy)
+    double* rre_out = nullptr;         // [cases][order (order + 1) / 2] Gram matrices (lazy)
+    double* rre_coef = nullptr;        // [cases][order] coefficients of the differences (lazy)
     double* case_out = nullptr;        // [cases][10] residual sums, then [cases][6] boundary sums
     void* fields = nullptr;            // [3 + 3 dim][S] of tau and u (lazy), FP64 or FP32
 };
@@ -71,6 +84,9 @@ struct CaseHostBC {
     double q[3];
     int base;
     int nf;
+    int nx, ny, nz;     // grid of the case
+    int wpr;            // row-table entries per (y, z) row: ceil(nx / 32)
+    int tab;            // first row-table entry of the case
 };
 
 size_t pop_size(int precision);    // bytes per stored population
@@ -90,6 +106,12 @@ cudaError_t launch_case_boundary(const Launch& L, cudaStream_t st);
 // per-case sums of (X - E)^2 etc. into case_out[c * 10 + v], E unchanged
 cudaError_t launch_case_extrap_norms(const Launch& L, cudaStream_t st);
 cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st);
+// reduced-rank extrapolation of order M (2..6): snapshot into slot, Gram
+// matrices of the M differences into rre_out, and the update from rre_coef
+cudaError_t launch_rre_snapshot(const Launch& L, int slot, cudaStream_t st);
+cudaError_t launch_rre_gram(const Launch& L, int order, cudaStream_t st);
+cudaError_t launch_rre_apply(const Launch& L, int order, cudaStream_t st);
+constexpr int kRreMaxOrder = 6;
 
 // Neighbour tables of one case built on the device from its dense
 // fluid-index map (index_of[cell] = index in the case or -1) and its fluid
@@ -99,6 +121,16 @@ cudaError_t launch_build_neighbours(int dim, const int64_t* fluid_cell, const in
                                     int ny, int nz, int periodic_x, int* nbr, int16_t* nbr16,
                                     unsigned long long* counts, cudaStream_t st);
 cudaError_t launch_fill16(int16_t* p, int64_t n, int16_t v, cudaStream_t st);
+
+// BF16 "TN" matrix product of the warm-start network on the tcgen05 tensor
+// cores (lbms_umma.cu): P[z][M][N] = A[M][K chunk z] . B[N][K chunk z]^T,
+// FP32.  Needs N a multiple of 64, (K / S) a multiple of 64, 16-byte aligned
+// operands with row strides a multiple of 8 elements; M is free.  *err is
+// raised if a wait in the kernel timed out.
+cudaError_t umma_gemm_init();
+bool umma_gemm_supported(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int S);
+cudaError_t umma_gemm_tn(const void* A, int lda, const void* B, int ldb, float* P, int M, int N, int K, int S,
+                         unsigned int* err, cudaStream_t st);
 
 // Read-only view of one case of a handle (for the warm-start network).
 struct CaseView {

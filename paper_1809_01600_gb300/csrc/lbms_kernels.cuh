@@ -26,6 +26,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -76,6 +77,68 @@ __device__ __forceinline__ void load_neighbours(const int* __restrict__ nbr, int
         if (1 + 4 * j + 1 < L::Q) nb[1 + 4 * j + 1] = v.y;
         if (1 + 4 * j + 2 < L::Q) nb[1 + 4 * j + 2] = v.z;
         if (1 + 4 * j + 3 < L::Q) nb[1 + 4 * j + 3] = v.w;
+    }
+}
+
+// Neighbours of a fluid cell from the per-row fluid bitmasks (kNbRowMask).
+// code = x | y << 11 | z << 21 of the cell (all ones for the padding cells
+// between cases, whose links are all solid).  Row-table entry (row, w) of a
+// case: .x/.y = bits 0..31/32..63 of a window of fluid flags of the voxels
+// x' = 32 w - 16 .. 32 w + 47 of that row (zero outside the grid), .z = the
+// fluid index the first fluid voxel at or after x' = 32 w - 16 has (or would
+// have).  Fluid cells are numbered in x-fastest order, so the index of a
+// fluid voxel is .z plus the number of fluid voxels before it in the window.
+// Link k pulls from (x, y, z) - e_k: one entry per source row gives the
+// sources x - 1, x and x + 1 of that row.  y and z are periodic; x is not
+// (beyond x = 0: inlet; beyond x = nx - 1: outlet).
+template <class L>
+__host__ __device__ constexpr bool row_used(int dy, int dz) {
+    for (int k = 1; k < L::Q; ++k)
+        if (-L::e(k, 1) == dy && -L::e(k, 2) == dz) return true;
+    return false;
+}
+
+template <class L>
+__device__ __forceinline__ void decode_neighbours(uint32_t code, const uint4* __restrict__ tab, int nx, int ny,
+                                                  int nz, int wpr, int (&nb)[L::Q]) {
+    if (code == 0xFFFFFFFFu) {
+#pragma unroll
+        for (int k = 1; k < L::Q; ++k) nb[k] = NB_SOLID;
+        return;
+    }
+    const int x = (int)(code & 2047u);
+    const int y = (int)((code >> 11) & 1023u);
+    const int z = (int)(code >> 21);
+    const int w = x >> 5;
+    const int b = (x & 31) + 16;                       // bit of x in the window, 16..47
+    const unsigned long long below = (1ull << b) - 1ull;
+    const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+    const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+    const int code_lo = x == 0 ? NB_INLET : NB_SOLID;        // source x - 1 not fluid
+    const int code_hi = x == nx - 1 ? NB_OUTLET : NB_SOLID;  // source x + 1 not fluid
+#pragma unroll
+    for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            if (!row_used<L>(dy, dz)) continue;
+            const int ys = dy == 0 ? y : (dy < 0 ? ym : yp);
+            const int zs = dz == 0 ? z : (dz < 0 ? zm : zp);
+            const uint4 e = __ldg(tab + (zs * ny + ys) * wpr + w);
+            const unsigned long long win = ((unsigned long long)e.y << 32) | e.x;
+            const int c = (int)e.z + __popcll(win & below);          // index x has (or would have)
+            const unsigned bits = (unsigned)(win >> (b - 1)) & 7u;   // fluid flags of x - 1, x, x + 1
+#pragma unroll
+            for (int k = 1; k < L::Q; ++k) {
+                if (-L::e(k, 1) != dy || -L::e(k, 2) != dz) continue;
+                const int dx = -L::e(k, 0);
+                if (dx < 0)
+                    nb[k] = (bits & 1u) ? c - 1 : code_lo;
+                else if (dx == 0)
+                    nb[k] = (bits & 2u) ? c : NB_SOLID;
+                else
+                    nb[k] = (bits & 4u) ? c + (int)((bits >> 1) & 1u) : code_hi;
+            }
+        }
     }
 }
 
@@ -214,6 +277,9 @@ struct CaseBC {
     typename Xv<XS>::T qout[3];       // outlet flux per node per step (Eq. 39)
     int base;                         // first fluid index of the case
     int nf;                           // fluid cells of the case
+    int nx, ny, nz;                   // grid (for the row-bitmask neighbour decode)
+    int wpr;                          // row-table entries per (y, z) row
+    int tab;                          // first row-table entry of the case
 };
 
 template <typename XS, typename P, typename NBT>
@@ -224,6 +290,8 @@ struct StepParams {
     XS* __restrict__ xout;
     const NBT* __restrict__ nbr;
     const int* __restrict__ nbr32;      // the 32-bit table (for NB16_FAR links)
+    const uint32_t* __restrict__ cell_code;   // coordinates of each cell (row-bitmask decode)
+    const uint4* __restrict__ rowtab;         // row tables of all cases (row-bitmask decode)
     const CaseBC<XS>* __restrict__ cases;
     const int* __restrict__ blk_case;   // case of each block of W cells
     int64_t S;
@@ -466,6 +534,7 @@ constexpr int prefetch_wave_divisor() {
 
 template <class L, typename XS, typename P, typename NBT>
 __device__ __forceinline__ void prefetch_ahead(const StepParams<XS, P, NBT>& p, int64_t wb, int lane) {
+    constexpr bool ROWMASK = std::is_same<NBT, RowMaskNb>::value;
     if (wb + 32 > p.S) return;
     constexpr int Q = L::Q;
     if constexpr (sizeof(P) == 2) {
@@ -479,80 +548,34 @@ __device__ __forceinline__ void prefetch_ahead(const StepParams<XS, P, NBT>& p, 
             for (int o = 0; o < nb; o += 128) prefetch_l2(a + o);
         }
     }
-    constexpr int NW = sizeof(NBT) == 2 ? nb16_width<L>() : nb_width<L>();
-    constexpr int NBYTES = 32 * NW * (int)sizeof(NBT);
-    const char* nbase = reinterpret_cast<const char*>(p.nbr + wb * NW);
-    for (int o = lane * 128; o < NBYTES; o += 32 * 128) prefetch_l2(nbase + o);
+    if constexpr (ROWMASK) {
+        if (lane == 0) prefetch_l2(p.cell_code + wb);     // 32 coordinates: one 128-byte line
+    } else {
+        constexpr int NW = sizeof(NBT) == 2 ? nb16_width<L>() : nb_width<L>();
+        constexpr int NBYTES = 32 * NW * (int)sizeof(NBT);
+        const char* nbase = reinterpret_cast<const char*>(p.nbr + wb * NW);
+        for (int o = lane * 128; o < NBYTES; o += 32 * 128) prefetch_l2(nbase + o);
+    }
 }
 
-// -------------------------------------------------------------------------
-// The same time step with one thread per fluid cell handling all three
-// species: the neighbour decode and the address selection of every link are
-// done once per cell instead of once per species thread.  The streamed
-// populations d_k wait for the coupling in shared memory (each thread reads
-// back only its own column, so no barrier), which keeps the register count
-// low enough for a useful number of resident warps.  Everything from the
-// gather to the store runs in storage units (h * kStore), so the FP16
-// scaling costs one multiply per species instead of one per population.
-template <class L, typename XS, typename P, typename NBT, int W, int MB, bool LIT>
-__global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P, NBT> p) {
+// Second half of a per-cell step, after the streamed populations of the
+// cell are in sD (storage units, d_k = f_k - w_k X_old, column t of a
+// [3][Q][W] array): boundary rules, gradient, Maxwell-Stefan coupling,
+// collision and stores.  acc[s] holds sum_k d_k, dxa the X differences on the
+// axis links.
+template <class L, typename XS, typename P, typename NBT, int W, bool LIT>
+__device__ __forceinline__ void cell_update(const StepParams<XS, P, NBT>& p, const CaseBC<XS>& cb, int t, int i,
+                                            const int (&nb)[L::Q], const Xv<XS> (&xo)[3],
+                                            typename Xv<XS>::T (&acc)[3],
+                                            const typename Xv<XS>::T (&dxa)[3][2 * L::DIM],
+                                            typename Xv<XS>::T (*sD)[L::Q][W]) {
     using T = typename Xv<XS>::T;
     using XV = Xv<XS>;
     constexpr int Q = L::Q;
     constexpr int DIM = L::DIM;
     constexpr T sc = T(Pop<T, P>::kStore);
-    __shared__ T sD[3][Q][W];
-    const int t = threadIdx.x;
-    const int i = blockIdx.x * W + t;
-    const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
     const int64_t S = p.S;
     const int S32 = (int)S;
-    if (p.pf_dist > 0) prefetch_ahead<L, XS, P, NBT>(p, i - (t & 31) + p.pf_dist, t & 31);
-    const P* hs[3];
-    const XS* xh[3];
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        hs[s] = p.hin + (int64_t)s * Q * S;
-        xh[s] = p.xin + (int64_t)s * S;
-    }
-
-    int nb[Q];
-    nb[0] = i;
-    if constexpr (sizeof(NBT) == 2)
-        load_neighbours<L>(p.nbr, p.nbr32, i, nb);
-    else
-        load_neighbours<L>(p.nbr, i, nb);
-
-    XV xo[3];
-    T acc[3], qs[3];
-    T dxa[3][2 * DIM];   // X(src) - X_old(x) on the axis links 1 .. 2 DIM
-#pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        xo[s] = XV::own_rows(xh[s], p.xin + (int64_t)(3 + s) * S, i);
-        const T h0 = Pop<T, P>::raw(hs[s] + i);
-        sD[s][0][t] = h0;
-        acc[s] = h0;
-        qs[s] = (LIT && p.c.outlet_extrap) ? T(0) : cb.qout[s] * sc;
-    }
-    constexpr T wx = T(weight_xplus<L>());
-#pragma unroll
-    for (int k = 1; k < Q; ++k) {
-        const int src = nb[k];
-        const bool fluid = src >= 0;
-        const int hoff = fluid ? k * S32 + src : opp<L>(k) * S32 + i;
-        const int xidx = fluid ? src : i;
-        const bool out = L::e(k, 0) == -1 && src == NB_OUTLET;
-#pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const T dx = xo[s].exch(xh[s][xidx]);
-            T val = T(weight<L>(k) * sc) * dx + Pop<T, P>::raw(hs[s] + hoff);
-            if (L::e(k, 0) == -1) val -= out ? T(weight<L>(opp<L>(k))) / wx * qs[s] : T(0);
-            sD[s][k][t] = val;
-            acc[s] += val;
-            if (k <= 2 * DIM) dxa[s][k - 1] = dx;
-        }
-    }
-
     bool at_outlet = false;
 #pragma unroll
     for (int k = 1; k < Q; ++k)
@@ -635,6 +658,79 @@ __global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P
         step_store(ho + i, Pop<T, P>::quant_raw(rest));
         xn[s].store_rows(p.xout + (int64_t)s * S, p.xout + (int64_t)(3 + s) * S, i);
     }
+}
+
+// -------------------------------------------------------------------------
+// The same time step with one thread per fluid cell handling all three
+// species: the neighbour decode and the address selection of every link are
+// done once per cell instead of once per species thread.  The streamed
+// populations d_k wait for the coupling in shared memory (each thread reads
+// back only its own column, so no barrier), which keeps the register count
+// low enough for a useful number of resident warps.  Everything from the
+// gather to the store runs in storage units (h * kStore), so the FP16
+// scaling costs one multiply per species instead of one per population.
+template <class L, typename XS, typename P, typename NBT, int W, int MB, bool LIT>
+__global__ void __launch_bounds__(W, MB) step_kernel_cell(const StepParams<XS, P, NBT> p) {
+    using T = typename Xv<XS>::T;
+    using XV = Xv<XS>;
+    constexpr int Q = L::Q;
+    constexpr int DIM = L::DIM;
+    constexpr T sc = T(Pop<T, P>::kStore);
+    __shared__ T sD[3][Q][W];
+    const int t = threadIdx.x;
+    const int i = blockIdx.x * W + t;
+    const CaseBC<XS>& cb = p.cases[__ldg(p.blk_case + blockIdx.x)];
+    const int64_t S = p.S;
+    const int S32 = (int)S;
+    if (p.pf_dist > 0) prefetch_ahead<L, XS, P, NBT>(p, i - (t & 31) + p.pf_dist, t & 31);
+    const P* hs[3];
+    const XS* xh[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        hs[s] = p.hin + (int64_t)s * Q * S;
+        xh[s] = p.xin + (int64_t)s * S;
+    }
+
+    int nb[Q];
+    nb[0] = i;
+    if constexpr (std::is_same<NBT, RowMaskNb>::value)
+        decode_neighbours<L>(__ldg(p.cell_code + i), p.rowtab + cb.tab, cb.nx, cb.ny, cb.nz, cb.wpr, nb);
+    else if constexpr (sizeof(NBT) == 2)
+        load_neighbours<L>(p.nbr, p.nbr32, i, nb);
+    else
+        load_neighbours<L>(p.nbr, i, nb);
+
+    XV xo[3];
+    T acc[3], qs[3];
+    T dxa[3][2 * DIM];   // X(src) - X_old(x) on the axis links 1 .. 2 DIM
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        xo[s] = XV::own_rows(xh[s], p.xin + (int64_t)(3 + s) * S, i);
+        const T h0 = Pop<T, P>::raw(hs[s] + i);
+        sD[s][0][t] = h0;
+        acc[s] = h0;
+        qs[s] = (LIT && p.c.outlet_extrap) ? T(0) : cb.qout[s] * sc;
+    }
+    constexpr T wx = T(weight_xplus<L>());
+#pragma unroll
+    for (int k = 1; k < Q; ++k) {
+        const int src = nb[k];
+        const bool fluid = src >= 0;
+        const int hoff = fluid ? k * S32 + src : opp<L>(k) * S32 + i;
+        const int xidx = fluid ? src : i;
+        const bool out = L::e(k, 0) == -1 && src == NB_OUTLET;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const T dx = xo[s].exch(xh[s][xidx]);
+            T val = T(weight<L>(k) * sc) * dx + Pop<T, P>::raw(hs[s] + hoff);
+            if (L::e(k, 0) == -1) val -= out ? T(weight<L>(opp<L>(k))) / wx * qs[s] : T(0);
+            sD[s][k][t] = val;
+            acc[s] += val;
+            if (k <= 2 * DIM) dxa[s][k - 1] = dx;
+        }
+    }
+
+    cell_update<L, XS, P, NBT, W, LIT>(p, cb, t, i, nb, xo, acc, dxa, sD);
 }
 
 // -------------------------------------------------------------------------
@@ -909,6 +1005,88 @@ __global__ void __launch_bounds__(kSegThreads) seg_extrapolate_kernel(XS* __rest
             store_x<XS>(X, S, s, i, xn);
             store_x<XS>(Xprev, S, s, i, xp + d);
             E[s * S + i] = xn;
+        }
+    }
+}
+
+// -------------------------------------------------------------------------
+// Reduced-rank extrapolation (RRE; Mesina 1977, Eddy 1979, in the form of
+// Sidi's vector extrapolation methods) over M + 1 snapshots x_0 .. x_M of X
+// taken W steps apart, in FP64: with u_a = x_{a+1} - x_a, the limit is
+// estimated as sum_j gamma_j x_j, where gamma minimises || sum_j gamma_j u_j ||
+// subject to sum_j gamma_j = 1 (solved on the host from the Gram matrix of
+// the u_a).  For an iteration whose error is a sum of at most M decaying
+// modes the estimate is the fixed point.  Snapshot j of a cycle sits in slot j
+// of `ring` ([slot][3][S] doubles).
+
+// Snapshot of X into ring slot `slot`, per segment.
+template <typename XS>
+__global__ void __launch_bounds__(kSegThreads) seg_snapshot_kernel(const XS* __restrict__ X, double* __restrict__ ring,
+                                                                   int64_t S, const int2* __restrict__ segs, int slot) {
+    const int2 sg = segs[blockIdx.x];
+    double* dst = ring + (int64_t)slot * 3 * S;
+    for (int j = threadIdx.x; j < sg.y; j += kSegThreads) {
+        const int i = sg.x + j;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) dst[s * S + i] = Xv<XS>::own(X, S, s, i).to_double();
+    }
+}
+
+// Partial Gram matrix of the differences u_a = x_{a+1} - x_a (a < M) over one
+// segment: entries (a, b), a <= b, packed row by row (M (M + 1) / 2 values).
+template <int M>
+__global__ void __launch_bounds__(kSegThreads) seg_gram_kernel(const double* __restrict__ ring, int64_t S,
+                                                               const int2* __restrict__ segs,
+                                                               double* __restrict__ partials) {
+    constexpr int NV = M * (M + 1) / 2;
+    const int2 sg = segs[blockIdx.x];
+    double acc[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) acc[v] = 0.0;
+    for (int j = threadIdx.x; j < sg.y; j += kSegThreads) {
+        const int i = sg.x + j;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            double x[M + 1], u[M];
+#pragma unroll
+            for (int a = 0; a <= M; ++a) x[a] = ring[((int64_t)a * 3 + s) * S + i];
+#pragma unroll
+            for (int a = 0; a < M; ++a) u[a] = x[a + 1] - x[a];
+            int v = 0;
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = a; b < M; ++b) acc[v++] += u[a] * u[b];
+        }
+    }
+    block_sum<NV>(acc, partials + (int64_t)blockIdx.x * NV);
+}
+
+// X += sum_a c_a u_a with the case's coefficients coef[case * M + a], in both
+// X copies (the step's and the lagged one); slot 0 takes the new X, the first
+// snapshot of the next cycle.
+template <typename XS, int M>
+__global__ void __launch_bounds__(kSegThreads) seg_rre_apply_kernel(XS* __restrict__ X, XS* __restrict__ Xprev,
+                                                                    double* __restrict__ ring, int64_t S,
+                                                                    const int2* __restrict__ segs,
+                                                                    const int* __restrict__ seg_case,
+                                                                    const double* __restrict__ coef) {
+    const int2 sg = segs[blockIdx.x];
+    const double* c = coef + (int64_t)seg_case[blockIdx.x] * M;
+    for (int j = threadIdx.x; j < sg.y; j += kSegThreads) {
+        const int i = sg.x + j;
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            double d = 0.0;
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+                d += c[a] * (ring[((int64_t)(a + 1) * 3 + s) * S + i] - ring[((int64_t)a * 3 + s) * S + i]);
+            const double x = Xv<XS>::own(X, S, s, i).to_double();
+            const double xp = Xv<XS>::own(Xprev, S, s, i).to_double();
+            const double xn = x + d;
+            store_x<XS>(X, S, s, i, xn);
+            store_x<XS>(Xprev, S, s, i, xp + d);
+            ring[s * S + i] = xn;
         }
     }
 }

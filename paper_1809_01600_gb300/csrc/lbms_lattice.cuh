@@ -87,6 +87,9 @@ enum : int {
     NB16_MAX_OFFSET = 32767
 };
 
+// Tag of the neighbour decode from per-row fluid bitmasks (no per-link table).
+struct RowMaskNb {};
+
 // Neighbour-table codes for a link whose source x - e_k is not a fluid cell.
 enum : int {
     NB_SOLID = -1,   // half-way bounce-back

@@ -34,6 +34,11 @@ void pack_t(const CaseHostBC& h, void* dst) {
     }
     c.base = h.base;
     c.nf = h.nf;
+    c.nx = h.nx;
+    c.ny = h.ny;
+    c.nz = h.nz;
+    c.wpr = h.wpr;
+    c.tab = h.tab;
     std::memcpy(dst, &c, sizeof(c));
 }
 
@@ -129,6 +134,7 @@ cudaError_t launch_step_variant(const Launch& L, int variant, cudaStream_t st) {
     LBMS_STEP_DISPATCH(false);
 }
 cudaError_t launch_step(const Launch& L, cudaStream_t st) { return launch_step_variant(L, L.variant, st); }
+
 cudaError_t launch_init(const Launch& L, int first, int count, cudaStream_t st) {
     LBMS_DISPATCH(init_t, L, first, count, st);
 }

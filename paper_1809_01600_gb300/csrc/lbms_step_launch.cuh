@@ -46,11 +46,15 @@ cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
     p.hout = static_cast<P*>(L.b.f[L.cur ^ 1]);
     p.xin = static_cast<const XS*>(L.b.X[L.cur]);
     p.xout = static_cast<XS*>(L.b.X[L.cur ^ 1]);
-    if constexpr (sizeof(NBT) == 2)
+    if constexpr (std::is_same<NBT, RowMaskNb>::value)
+        p.nbr = nullptr;
+    else if constexpr (sizeof(NBT) == 2)
         p.nbr = L.b.nbr16;
     else
         p.nbr = L.b.nbr;
     p.nbr32 = L.b.nbr;
+    p.cell_code = L.b.cell_code;
+    p.rowtab = L.b.rowtab;
     p.cases = static_cast<const CaseBC<XS>*>(L.b.cases);
     p.blk_case = L.b.blk_case[variant];
     p.S = L.S;
@@ -66,7 +70,9 @@ cudaError_t step_w(const Launch& L, int variant, cudaStream_t st) {
 
 template <class Lat, typename XS, typename P, bool LIT>
 cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
-    static_assert(kStepVariants == 8 && kVariantPerCell[6] && kVariantPerCell[7] && !kVariantPerCell[5],
+    static_assert(kStepVariants == 10 && kVariantPerCell[6] && kVariantPerCell[7] && !kVariantPerCell[5] &&
+                      kVariantNb[8] == kNbRowMask && kVariantNb[9] == kNbRowMask && kVariantPerCell[8] &&
+                      kVariantPerCell[9],
                   "variant table");
     switch (variant) {
         case 0: return step_w<Lat, XS, P, int, kVariantCells[0], kVariantMinBlocks[0], false, LIT>(L, 0, st);
@@ -76,7 +82,9 @@ cudaError_t step_t(const Launch& L, int variant, cudaStream_t st) {
         case 4: return step_w<Lat, XS, P, int16_t, kVariantCells[4], kVariantMinBlocks[4], false, LIT>(L, 4, st);
         case 5: return step_w<Lat, XS, P, int16_t, kVariantCells[5], kVariantMinBlocks[5], false, LIT>(L, 5, st);
         case 6: return step_w<Lat, XS, P, int, kVariantCells[6], kVariantMinBlocks[6], true, LIT>(L, 6, st);
-        default: return step_w<Lat, XS, P, int, kVariantCells[7], kVariantMinBlocks[7], true, LIT>(L, 7, st);
+        case 7: return step_w<Lat, XS, P, int, kVariantCells[7], kVariantMinBlocks[7], true, LIT>(L, 7, st);
+        case 8: return step_w<Lat, XS, P, RowMaskNb, kVariantCells[8], kVariantMinBlocks[8], true, LIT>(L, 8, st);
+        default: return step_w<Lat, XS, P, RowMaskNb, kVariantCells[9], kVariantMinBlocks[9], true, LIT>(L, 9, st);
     }
 }
 

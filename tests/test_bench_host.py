@@ -10,16 +10,20 @@ import bench  # noqa: E402
 
 
 def test_bytes_per_cell():
-    # one read and one write of 3 x Q populations and of the 8-byte X word
-    assert bench.bytes_per_cell(3, "fp32") == 3 * (2 * 19 * 4 + 16) == 504
-    assert bench.bytes_per_cell(3, "fp16") == 3 * (2 * 19 * 2 + 16) == 276
+    # one read and one write of 3 x Q populations and of X at the method's
+    # precision: 160 B per species-update (D3Q19 FP32), 84 B (16-bit storage)
+    assert bench.bytes_per_cell(3, "fp32") == 3 * 160 == 480
+    assert bench.bytes_per_cell(3, "fp16") == 3 * 84 == 252
     assert bench.bytes_per_cell(2, "fp64") == 3 * (2 * 9 * 8 + 16) == 480
+    assert bench.bytes_per_cell(2, "fp32") == 3 * 80
 
 
 def test_variant_key_and_traffic_lookup(tmp_path, monkeypatch):
     info = type("I", (), dict(tile_cells=64, tile_min_blocks=8, threads_per_cell=1, neighbour_bits=32))()
     key = bench.variant_key(info)
     assert key == "64x8/t1/nb32"
+    rowmask = type("I", (), dict(tile_cells=64, tile_min_blocks=8, threads_per_cell=1, neighbour_bits=1))()
+    assert bench.variant_key(rowmask) == "64x8/t1/nb1"
     sha = bench.kernel_source_sha()
     assert len(sha) == 16 and sha == bench.kernel_source_sha()
     prof = tmp_path / "profiles"

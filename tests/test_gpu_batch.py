@@ -88,12 +88,13 @@ def test_batch_rejects_mixed_dims(L):
     assert e.value.status == L.LBMS_EINVAL
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("variant", list(range(1, 11)))
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-13), ("fp32", 1e-7)])
 def test_every_step_variant_gives_the_same_fields(L, variant, precision, tol):
-    """All tile shapes, both neighbour-table formats and both thread mappings
-    (one thread per cell and species, one per cell) the autotuner may pick
-    compute the same step (to rounding of FMA contraction)."""
+    """All tile shapes, all three neighbour lookups (32-bit indices, 16-bit
+    offsets, row bitmasks) and both thread mappings (one thread per cell and
+    species, one per cell) the autotuner may pick compute the same step (to
+    rounding of FMA contraction)."""
     c = cases.porous((12, 14, 30), radius=2, porosity=0.5, seed=71, current_A_cm2=1.5)
     ref = L.Solver.from_case(c, precision=precision, step_variant=1)
     s = L.Solver.from_case(c, precision=precision, step_variant=variant)
@@ -101,7 +102,7 @@ def test_every_step_variant_gives_the_same_fields(L, variant, precision, tol):
         h.set_bc(c.x_in, c.current_A_cm2)
         h.step(77)
     i = s.info()
-    assert i.neighbour_bits == (16 if 4 <= variant <= 6 else 32)
+    assert i.neighbour_bits == (16 if 4 <= variant <= 6 else (1 if variant >= 9 else 32))
     assert i.threads_per_cell == (1 if variant >= 7 else 3)
     assert np.abs(s.fields() - ref.fields()).max() <= tol
 
@@ -121,14 +122,52 @@ def test_far_links_of_the_16_bit_table(L, variant):
     assert np.abs(s.fields() - o.X)[:, f].max() <= 1e-11
 
 
+@pytest.mark.parametrize("variant", [9, 10])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-11), ("fp32", 1e-6), ("fp16", 2e-5)])
+def test_row_bitmask_decode_against_oracle(L, variant, precision, tol):
+    """The neighbour decode from per-row fluid bitmasks (variants 9-10): a
+    batch of a 3-D anode wider than one 32-voxel word (x = 70, so windows
+    straddle words), with periodic wraps in y and z, and a 2-D strip one
+    voxel high (ny = 1: every y neighbour is the cell itself), against the
+    oracle."""
+    for cs in ([cases.porous((6, 9, 70), radius=2, porosity=0.5, seed=73, current_A_cm2=1.5),
+                cases.porous((5, 7, 33), radius=2, porosity=0.6, seed=74, current_A_cm2=0.5)],
+               [cases.open_channel(40, 1, current_A_cm2=2.0),
+                cases.porous((11, 65), radius=2, porosity=0.55, seed=75, current_A_cm2=1.0)]):
+        b = L.Batch.from_cases(cs, precision=precision, step_variant=variant)
+        for k, c in enumerate(cs):
+            b.set_bc(c.x_in, c.current_A_cm2, case=k)
+        assert b.info().neighbour_bits == 1
+        b.step(60)
+        for k, c in enumerate(cs):
+            o = Oracle(c)
+            o.step(60)
+            f = ~c.solid
+            assert np.abs(b.fields(k) - o.X)[:, f].max() <= tol, (c.name, precision)
+        b.close()
+
+
+def test_row_bitmask_variant_needs_a_box_open_in_x(L):
+    c = cases.porous((8, 12), radius=2, porosity=0.6, seed=61).with_(periodic_x=True)
+    s = L.Solver.from_case(c, precision="fp64", step_variant=9)
+    with pytest.raises(L.LbmsError) as e:
+        s.set_bc(c.x_in, 0.0)
+    assert e.value.status == L.LBMS_EINVAL and "row-bitmask" in str(e.value)
+    s.close()
+    s = L.Solver.from_case(c, precision="fp64")      # the autotuner skips those variants
+    s.set_bc(c.x_in, 0.0)
+    assert s.info().neighbour_bits in (16, 32)
+    s.close()
+
+
 @pytest.mark.slow
 def test_full_sweep_launch_sampled_cases_against_oracle(L):
-    """The benchmark's batched sweep at full size (8 2-D + 8 3-D seeded
-    microstructures x 8 operating points, 128 cases, ~61M fluid cells, one
-    FP32 launch per lattice and step): two sampled cases - the largest 3-D
-    and the largest 2-D grid - start from non-uniform fields, and after two
-    batched steps every one of their cells matches the oracle run on that
-    case alone."""
+    """A full-size batched sweep (8 2-D + 8 3-D seeded microstructures of the
+    benchmark's recipe x 8 operating points, 128 cases, ~61M fluid cells, one
+    FP32 launch per lattice and step; the benchmark itself runs 32 + 32):
+    two sampled cases - the largest 3-D and the largest 2-D grid - start
+    from non-uniform fields, and after two batched steps every one of their
+    cells matches the oracle run on that case alone."""
     import bench
     args = type("A", (), dict(sweep_2d=8, sweep_3d=8, sweep_scale=1.0, sweep_points=8))()
     groups = bench.sweep_cases(args)
