@@ -16,8 +16,9 @@
  * the cumulative resistance int_0^x dx / porosity(x) (normalised), the
  * current density and the inlet composition.  The network maps the row to
  * 100 (X_steady - X_profile) for the three species.  Hidden layers use ReLU;
- * weights are stored in BF16 for the tensor-core matrix products (FP32
- * accumulation) with FP32 master copies updated by Adam.
+ * weights are stored in BF16 for the tensor-core matrix products (tcgen05,
+ * FP32 accumulation in tensor memory) with FP32 master copies updated by
+ * Adam.
  *
  * All functions return an lbms_status and never abort; buffers are host
  * memory owned by the caller unless stated otherwise.  A net is not thread
@@ -46,6 +47,19 @@ lbms_status lbms_net_create(int width, int depth, uint64_t seed, lbms_net **out)
  * cells and, as the target, the handle's current mole fractions of that case
  * (call it on a steady state).  The case must have boundary data. */
 lbms_status lbms_net_add_sample(lbms_net *net, lbms_ctx *ctx, int case_index);
+
+/* The feature rows the network sees for one case of a handle (the rows
+ * lbms_net_add_sample and lbms_net_warm_start build on the GPU), for
+ * inspection and tests: rows [n_rows][LBMS_NET_FEATURES] BF16 bit patterns,
+ * one per fluid cell in x-fastest order; n_rows must equal the case's fluid
+ * cell count.  Columns: 0-2 the Section 4.1 profile X at the cell's x, 3
+ * x / (nx - 1), 4-6 the fluid fraction of the (2h+1)^dim boxes with h = 1, 3,
+ * 7 around the cell (clamped at the ends of x, periodic in y and z), 7 the
+ * current density / 2 (A/cm^2), 8-10 the inlet X, 11 column 3 times column
+ * 7, 12 the fluid fraction phi(x) of the cell's x-plane (at least one cell),
+ * 13 the trapezoidal integral of 1 / phi from 0 to x over its value at
+ * nx - 1, 14 1 / (4 phi(x)), 15 one, 16-63 zero. */
+lbms_status lbms_net_features(lbms_net *net, lbms_ctx *ctx, int case_index, uint16_t *rows, int64_t n_rows);
 
 /* iters steps of Adam (beta 0.9 / 0.999, eps 1e-8) on mean-square error over
  * batches of `batch` rows (a multiple of 64) drawn uniformly with replacement
@@ -78,6 +92,18 @@ lbms_status lbms_net_get(const lbms_net *net, int what, float *buf, int64_t n);
 lbms_status lbms_net_set(lbms_net *net, const float *params, int64_t n);
 
 lbms_status lbms_net_info(const lbms_net *net, int64_t *n_params, int64_t *n_samples);
+
+/* Which kernel computes the network's matrix products.  AUTO: the tcgen05
+ * tensor-core kernel (operands staged by TMA, FP32 accumulators in tensor
+ * memory) for every product whose sizes it takes (N and each K chunk
+ * multiples of 64), the mma.sync kernel for the others; TCGEN05: the
+ * tcgen05 kernel only (a product it cannot take is LBMS_EINVAL); MMA_SYNC:
+ * the mma.sync kernel only.  lbms_net_gemm_calls counts the products each
+ * kernel has computed since the net was created.  A timed-out wait inside
+ * the tcgen05 kernel is reported as LBMS_ECUDA by the call that ran it. */
+enum { LBMS_NET_GEMM_AUTO = 0, LBMS_NET_GEMM_TCGEN05 = 1, LBMS_NET_GEMM_MMA_SYNC = 2 };
+lbms_status lbms_net_set_gemm(lbms_net *net, int kind);
+lbms_status lbms_net_gemm_calls(const lbms_net *net, int64_t *tcgen05_calls, int64_t *mma_sync_calls);
 const char *lbms_net_last_error(const lbms_net *net);
 void lbms_net_destroy(lbms_net *net);
 

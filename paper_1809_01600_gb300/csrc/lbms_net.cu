@@ -395,6 +395,9 @@ struct lbms_net {
     int64_t n_rows = 0, cap = 0;
     int64_t step = 0;
     uint64_t seed = 0;
+    unsigned int* gemm_err = nullptr;       // raised by the tensor-core GEMM on a timed-out wait
+    int gemm_kind = LBMS_NET_GEMM_AUTO;
+    int64_t tcgen05_calls = 0, mma_sync_calls = 0;
     std::vector<void*> allocs;
     std::string err;
 };
@@ -441,12 +444,35 @@ int64_t n_params(const lbms_net* n) {
 }
 
 // P[z] = A . B^T with the checks the kernel relies on.
+// P = A . B^T on the fifth-generation tensor cores (tcgen05, lbms_umma.cu)
+// whenever the shape allows it; otherwise, or when forced, the mma.sync
+// kernel above.
 lbms_status gemm(lbms_net* n, const bf16* A, int lda, const bf16* B, int ldb, int M, int N, int K, int S) {
-    if (M % kTM || N % kTN || K % (kTK * S) || lda % 8 || ldb % 8 || (size_t)S * M * N > n->P_floats)
+    if ((size_t)S * M * N > n->P_floats)
+        return nfail(n, LBMS_EINVAL, "internal GEMM shape %d x %d x %d (split %d) exceeds the partials", M, N, K, S);
+    if (n->gemm_kind != LBMS_NET_GEMM_MMA_SYNC && lbms::umma_gemm_supported(A, lda, B, ldb, M, N, K, S) &&
+        lbms::umma_gemm_init() == cudaSuccess) {
+        NCK(lbms::umma_gemm_tn(A, lda, B, ldb, n->P, M, N, K, S, n->gemm_err, 0), "tensor-core gemm");
+        ++n->tcgen05_calls;
+        return LBMS_OK;
+    }
+    if (n->gemm_kind == LBMS_NET_GEMM_TCGEN05)
+        return nfail(n, LBMS_EINVAL, "GEMM %d x %d x %d (split %d) is not supported by the tcgen05 kernel", M, N, K, S);
+    if (M % kTM || N % kTN || K % (kTK * S) || lda % 8 || ldb % 8)
         return nfail(n, LBMS_EINVAL, "internal GEMM shape %d x %d x %d (split %d) not tileable", M, N, K, S);
     gemm_tn_kernel<<<dim3(N / kTN, M / kTM, S), 128>>>(A, lda, B, ldb, n->P, M, N, K / S);
     NCK(cudaGetLastError(), "gemm");
+    ++n->mma_sync_calls;
     return LBMS_OK;
+}
+
+// Reads and clears the tensor-core GEMM's error flag (after the device work).
+lbms_status check_gemm(lbms_net* n) {
+    unsigned int f = 0;
+    NCK(cudaMemcpy(&f, n->gemm_err, sizeof(f), cudaMemcpyDeviceToHost), "GEMM flag");
+    if (!f) return LBMS_OK;
+    NCK(cudaMemset(n->gemm_err, 0, sizeof(f)), "GEMM flag");
+    return nfail(n, LBMS_ECUDA, "tensor-core GEMM: an mbarrier wait timed out (flag %u)", f);
 }
 
 lbms_status transpose(lbms_net* n, const bf16* in, bf16* out, int R, int C) {
@@ -486,9 +512,10 @@ lbms_status backward_step(lbms_net* n, int R, double lr, double* loss) {
     NCK(cudaGetLastError(), "loss");
     int cur = 0;
     // split of the R-long reduction of the weight gradients: chunks of >= 512
-    // rows, a divisor of R / 32 so that every chunk is whole 32-row steps
+    // rows, a divisor of R / 64 so that every chunk is whole 64-row steps (the
+    // K step of the tcgen05 kernel; two of the mma.sync kernel's)
     int S = std::max(1, std::min(16, R / 512));
-    while (S > 1 && (R / 32) % S) --S;
+    while (S > 1 && (R / 64) % S) --S;
     for (int l = L - 1; l >= 0; --l) {
         const int O = n->out[l], I = n->in[l];
         // weight gradient: dZ^T [O][R] . act^T [I][R]
@@ -684,6 +711,7 @@ lbms_status lbms_net_create(int width, int depth, uint64_t seed, lbms_net** out)
     n->Y = nalloc<float>(n, (size_t)kMaxRows * kOutPad);
     n->T = nalloc<float>(n, (size_t)kMaxRows * 4);
     n->loss = nalloc<double>(n, 1);
+    n->gemm_err = nalloc<unsigned int>(n, 1);
     for (void* p : n->allocs) ok = ok && p;
     if (!ok) {
         lbms_net_destroy(n);
@@ -699,6 +727,7 @@ lbms_status lbms_net_create(int width, int depth, uint64_t seed, lbms_net** out)
                 w[e] = (float)(a * (2.0 * unit_double(seed * 0x100000001ull + (uint64_t)l * 0x1000000000ull + e) - 1.0));
         }
         if (cudaMemcpy(n->W[l], w.data(), nw * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) ok = false;
+        cudaMemset(n->gemm_err, 0, sizeof(unsigned int));
         cudaMemset(n->mW[l], 0, nw * sizeof(float));
         cudaMemset(n->vW[l], 0, nw * sizeof(float));
         cudaMemset(n->gW[l], 0, nw * sizeof(float));
@@ -732,6 +761,19 @@ lbms_status lbms_net_info(const lbms_net* n, int64_t* np, int64_t* ns) {
     if (!n) return LBMS_EINVAL;
     if (np) *np = n_params(n);
     if (ns) *ns = n->n_rows;
+    return LBMS_OK;
+}
+
+lbms_status lbms_net_features(lbms_net* n, lbms_ctx* ctx, int k, uint16_t* rows, int64_t n_rows) {
+    if (!n || !ctx || !rows) return LBMS_EINVAL;
+    lbms::CaseView v;
+    if (!lbms::case_view(ctx, k, &v)) return nfail(n, LBMS_EINVAL, "case index %d out of range", k);
+    if (n_rows != v.nf) return nfail(n, LBMS_EINVAL, "case %d has %d fluid cells, the buffer holds %lld rows", k, v.nf,
+                                     (long long)n_rows);
+    CaseFeatures F;
+    lbms_status st = case_features(n, ctx, k, F);
+    if (st != LBMS_OK) return st;
+    NCK(cudaMemcpy(rows, F.rows, (size_t)v.nf * kF * sizeof(bf16), cudaMemcpyDeviceToHost), "feature rows");
     return LBMS_OK;
 }
 
@@ -787,6 +829,8 @@ lbms_status lbms_net_train(lbms_net* n, int iters, int batch, double lr, double*
         }
     }
     NCK(cudaDeviceSynchronize(), "train");
+    lbms_status gst = check_gemm(n);
+    if (gst != LBMS_OK) return gst;
     if (last_loss) *last_loss = nt ? tail / nt : 0.0;
     return LBMS_OK;
 }
@@ -799,6 +843,8 @@ lbms_status lbms_net_forward(lbms_net* n, const uint16_t* features, int rows, fl
     if (st != LBMS_OK) return st;
     std::vector<float> y((size_t)rows * kOutPad);
     NCK(cudaMemcpy(y.data(), n->Y, y.size() * sizeof(float), cudaMemcpyDeviceToHost), "read output");
+    st = check_gemm(n);
+    if (st != LBMS_OK) return st;
     for (int r = 0; r < rows; ++r)
         for (int s = 0; s < kOut; ++s) out[(size_t)r * kOut + s] = y[(size_t)r * kOutPad + s];
     return LBMS_OK;
@@ -818,6 +864,24 @@ lbms_status lbms_net_train_batch(lbms_net* n, const uint16_t* features, const fl
     st = backward_step(n, rows, lr, loss);
     if (st != LBMS_OK) return st;
     NCK(cudaDeviceSynchronize(), "train batch");
+    return check_gemm(n);
+}
+
+lbms_status lbms_net_set_gemm(lbms_net* n, int kind) {
+    if (!n || (kind != LBMS_NET_GEMM_AUTO && kind != LBMS_NET_GEMM_TCGEN05 && kind != LBMS_NET_GEMM_MMA_SYNC))
+        return LBMS_EINVAL;
+    if (kind == LBMS_NET_GEMM_TCGEN05) {
+        const cudaError_t e = lbms::umma_gemm_init();
+        if (e != cudaSuccess) return nfail(n, LBMS_ECUDA, "tcgen05 GEMM unavailable: %s", cudaGetErrorString(e));
+    }
+    n->gemm_kind = kind;
+    return LBMS_OK;
+}
+
+lbms_status lbms_net_gemm_calls(const lbms_net* n, int64_t* tcgen05, int64_t* mma_sync) {
+    if (!n) return LBMS_EINVAL;
+    if (tcgen05) *tcgen05 = n->tcgen05_calls;
+    if (mma_sync) *mma_sync = n->mma_sync_calls;
     return LBMS_OK;
 }
 

@@ -1,0 +1,285 @@
+// BF16 matrix product of the warm-start network on the fifth-generation
+// tensor cores: P[z][M][N] = sum_{k in chunk z} A[m][k] B[n][k] with A [M][K]
+// and B [N][K] both K-contiguous ("TN"), FP32 accumulation.
+//
+// One CTA of 128 threads per 128 x 64 output tile and K chunk.  Operand
+// tiles of 64 K-elements (one 128-byte swizzle span of BF16) are staged in
+// shared memory by TMA (cp.async.bulk.tensor, 128-byte swizzle) through a
+// four-stage ring of mbarriers; one thread issues tcgen05.mma (M = 128,
+// N = 64, K = 16 per instruction) into a TMEM accumulator of 64 columns, and
+// tcgen05.commit releases each stage when the products reading it are done.
+// The four warps then read their 32 TMEM lanes (rows) with tcgen05.ld and
+// store FP32.  Rows and K beyond the operands' extents are zero-filled by
+// TMA, so M and K need no padding; N is a multiple of 64.
+//
+// Every mbarrier wait is bounded (about 2 s on the global timer): on a
+// timeout the kernel raises *err, still waits (bounded) for the copies it
+// issued, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "lbms_internal.h"
+
+namespace lbms {
+namespace {
+
+constexpr int kUM = 128;                       // output rows per CTA (UMMA M)
+constexpr int kUN = 64;                        // output columns per CTA (UMMA N)
+constexpr int kUK = 64;                        // K per stage: 64 BF16 = one 128-byte swizzle row
+constexpr int kStages = 4;
+constexpr int kABytes = kUM * kUK * 2;         // 16 KiB
+constexpr int kBBytes = kUN * kUK * 2;         // 8 KiB
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kTmemCols = 64;                  // FP32 accumulator: 128 lanes x 64 columns
+constexpr size_t kSmemBytes = 1024 + (size_t)kStages * kStageBytes + 256;
+constexpr uint64_t kWaitNs = 2000000000ull;    // bound of every mbarrier wait
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32 (bits 4-5 = 1),
+// A and B BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kUN >> 3) << 17) |
+                            ((uint32_t)(kUM >> 4) << 24);
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Waits for the completion of the phase of parity `par`; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t par) {
+    const uint32_t a = smem_u32(bar);
+    const uint64_t t0 = global_ns();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(par)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile whose rows are
+// 128 bytes (64 BF16) in the 128-byte swizzle written by TMA: start address
+// >> 4 (bits 0-13), leading offset 16 B (unused with this swizzle, bits
+// 16-29), 8-row groups 1024 B apart (bits 32-45), the fixed 0b001 of bits
+// 46-48, swizzle mode 2 = 128 B (bits 61-63).  The tile base is 1024-byte
+// aligned; the k-th 16-element slice starts 32 k bytes further.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            tmem),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+        "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+          "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB,
+                                                           float* __restrict__ P, int M, int N, int kchunk,
+                                                           unsigned int* __restrict__ err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kStages * kStageBytes);
+    uint64_t* empty = full + kStages;
+    uint64_t* done = empty + kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * kUN, m0 = blockIdx.y * kUM, k0 = blockIdx.z * kchunk;
+    const int nk = kchunk / kUK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;                        // stages whose loads were issued
+        auto load = [&](int kt) {
+            const int s = kt % kStages;
+            uint8_t* sa = base + (size_t)s * kStageBytes;
+            mbar_expect_tx(&full[s], kStageBytes);
+            tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
+            tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
+            ++issued;
+        };
+        for (int kt = 0; kt < nk && kt < kStages; ++kt) load(kt);
+        int consumed = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kStages;
+            const uint32_t ph = (uint32_t)(kt / kStages) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+                ok = false;
+                break;
+            }
+            ++consumed;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = smem_u32(base + (size_t)s * kStageBytes);
+            const uint32_t b = a + kABytes;
+#pragma unroll
+            for (int j = 0; j < kUK / 16; ++j)
+                umma_f16(tmem, sw128_desc(a + 32 * j), sw128_desc(b + 32 * j), (kt | j) != 0 ? 1u : 0u);
+            umma_commit(&empty[s]);
+            if (kt + kStages < nk) {
+                if (!mbar_wait(&empty[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                load(kt + kStages);
+            }
+        }
+        umma_commit(done);                     // arrives once every product issued above is complete
+        if (!ok) {
+            atomicOr(err, 1u);
+            // copies still in flight land in their stages before the CTA exits
+            for (int kt = consumed; kt < issued; ++kt) mbar_wait(&full[kt % kStages], (uint32_t)(kt / kStages) & 1u);
+        }
+    }
+    __syncwarp();
+    const bool got = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!got) {
+        if (lane == 0) atomicOr(err, 2u);
+    } else {
+        // warp w holds TMEM lanes (rows) 32 w .. 32 w + 31: row m0 + 32 w + lane, 64 columns
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        uint32_t v0[32], v1[32];
+        tmem_ld32(taddr, v0);
+        tmem_ld32(taddr + 32, v1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = m0 + 32 * warp + lane;
+        if (row < M) {
+            float4* dst = reinterpret_cast<float4*>(P + (int64_t)blockIdx.z * M * N + (int64_t)row * N + n0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dst[q] = make_float4(__uint_as_float(v0[4 * q]), __uint_as_float(v0[4 * q + 1]),
+                                     __uint_as_float(v0[4 * q + 2]), __uint_as_float(v0[4 * q + 3]));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dst[8 + q] = make_float4(__uint_as_float(v1[4 * q]), __uint_as_float(v1[4 * q + 1]),
+                                         __uint_as_float(v1[4 * q + 2]), __uint_as_float(v1[4 * q + 3]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_once;
+cudaError_t g_init = cudaErrorNotReady;
+
+void init_once() {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        g_init = e != cudaSuccess ? e : cudaErrorNotSupported;
+        return;
+    }
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    g_init = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+}
+
+// 2-D tensor map of a K-contiguous BF16 operand: inner extent K, `rows`
+// rows `ld` elements apart, boxes of 64 x box_rows with the 128-byte swizzle;
+// elements outside the extents read as zero.
+bool make_map(CUtensorMap* map, const void* base, int K, int rows, int ld, int box_rows) {
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kUK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t umma_gemm_init() {
+    std::call_once(g_once, init_once);
+    return g_init;
+}
+
+bool umma_gemm_supported(const void* A, int lda, const void* B, int ldb, int M, int N, int K, int S) {
+    if (M < 1 || N < kUN || N % kUN || K < 1 || S < 1 || K % S || (K / S) % kUK) return false;
+    if (lda % 8 || ldb % 8 || lda < K || ldb < K) return false;
+    if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15u) return false;
+    return (M + kUM - 1) / kUM <= 65535 && S <= 65535;
+}
+
+cudaError_t umma_gemm_tn(const void* A, int lda, const void* B, int ldb, float* P, int M, int N, int K, int S,
+                         unsigned int* err, cudaStream_t st) {
+    cudaError_t e = umma_gemm_init();
+    if (e != cudaSuccess) return e;
+    if (!umma_gemm_supported(A, lda, B, ldb, M, N, K, S)) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, A, K, M, lda, kUM) || !make_map(&mb, B, K, N, ldb, kUN)) return cudaErrorInvalidValue;
+    const dim3 grid(N / kUN, (M + kUM - 1) / kUM, S);
+    umma_gemm_kernel<<<grid, 128, kSmemBytes, st>>>(ma, mb, P, M, N, K / S, err);
+    return cudaGetLastError();
+}
+
+}  // namespace lbms

@@ -6,6 +6,7 @@ same steady state as from the uniform start."""
 import numpy as np
 import pytest
 
+import closed_forms as cf
 from workloads import cases
 
 pytestmark = pytest.mark.gpu
@@ -64,26 +65,50 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
-def test_forward_matches_reference(L):
-    net, layers = _random_net(L, 128, 2, 5)
-    bits, x = _features(L, 256, 6)
+GEMMS = ["tcgen05", "mma_sync"]
+
+
+def _used_only(net, kind):
+    tc, ms = net.gemm_calls()
+    return (tc > 0 and ms == 0) if kind == "tcgen05" else (ms > 0 and tc == 0)
+
+
+@pytest.mark.parametrize("gemm", GEMMS)
+@pytest.mark.parametrize("width,rows", [(128, 256), (704, 192)])
+def test_forward_matches_reference(L, gemm, width, rows):
+    """Forward pass on the tcgen05 (TMA + TMEM) and the mma.sync products;
+    width 704 and 192 rows leave partial 128-row tiles (zero-filled by TMA)."""
+    net, layers = _random_net(L, width, 2, 5)
+    net.set_gemm(gemm)
+    bits, x = _features(L, rows, 6)
     out = net.forward(bits)
     ref, _, _ = _reference(layers, x)
-    assert out.shape == (256, 3)
+    assert out.shape == (rows, 3)
     assert _rel(out, ref) < 5e-3
+    assert np.all(np.abs(out - ref) <= 2e-2 * np.abs(ref) + 1e-2 * np.abs(ref).max())
+    assert _used_only(net, gemm)
 
 
-def test_gradients_and_loss_match_reference(L):
+@pytest.mark.parametrize("gemm", GEMMS)
+def test_gradients_and_loss_match_reference(L, gemm):
     net, layers = _random_net(L, 128, 2, 7)
+    net.set_gemm(gemm)
     bits, x = _features(L, 512, 8)
     t = np.random.default_rng(9).standard_normal((512, 3)).astype(np.float32)
     loss = net.train_batch(bits, t, lr=0.0)
+    assert _used_only(net, gemm)
     _, ref_loss, ref_grads = _reference(layers, x, t)
     assert loss == pytest.approx(ref_loss, rel=1e-4)
     got = net.get(1)
     for (gW, gb), (rW, rb) in zip(got, ref_grads):
         assert _rel(gW, rW) < 3e-2
         assert _rel(gb, rb) < 3e-2
+        # element by element: the device rounds the output and hidden-layer
+        # gradients to BF16 (2^-8 relative) before the weight-gradient
+        # products, so each entry is within a few per cent of its own size
+        # plus a few per cent of the layer's largest entry
+        for g, r in ((gW, rW), (gb, rb)):
+            assert np.all(np.abs(g - r) <= 3e-2 * np.abs(r) + 2e-2 * np.abs(r).max())
     # lr = 0 leaves the parameters as they were
     for (W, b), (W0, b0) in zip(net.get(0), layers):
         assert np.array_equal(W, W0) and np.array_equal(b, b0)
@@ -153,3 +178,89 @@ def test_warm_start_predicts_better_than_the_profile_and_converges_to_the_same_s
     # the LBM, not the network, decides the result
     warm.run_to_residual(1e-12, 3_000_000)
     assert np.abs(warm.fields() - Xs)[:, f].max() < 1e-7
+
+
+def _reference_features(case):
+    """The feature rows of lbms_net_features computed independently in
+    numpy: the closed-form 1-D profile (Eq. 19 with the outlet fluxes of
+    Eq. 39 held across the anode, closed_forms) at each cell's x, box-filter
+    fluid fractions, the plane porosity and the cumulative resistance."""
+    solid = case.solid
+    nz, ny, nx = solid.shape
+    m = (~solid).astype(np.float64)
+    g = case.gas
+    xs = np.arange(nx) * case.length_x / (nx - 1)
+    prof = cf.anode_1d(xs, case.x_in, case.current_A_cm2, g.T, g.p, g.pore_diameter, g.eps_over_tau)
+    boxes = []
+    for h in (1, 3, 7):
+        sx = np.zeros_like(m)
+        cx = np.zeros(nx)
+        for d in range(-h, h + 1):
+            lo, hi = max(0, -d), min(nx, nx - d)          # x + d stays inside [0, nx)
+            sx[:, :, lo:hi] += m[:, :, lo + d:hi + d]
+            cx[lo:hi] += 1
+        sy = sum(np.roll(sx, -d, axis=1) for d in range(-h, h + 1))
+        hz = h if nz > 1 else 0
+        sz = sum(np.roll(sy, -d, axis=0) for d in range(-hz, hz + 1))
+        boxes.append(sz / (cx[None, None, :] * (2 * h + 1) * (2 * hz + 1)))
+    phi = np.maximum(m.sum(axis=(0, 1)) / (ny * nz), 1.0 / (ny * nz))
+    res = np.concatenate([[0.0], np.cumsum(0.5 * (1.0 / phi[:-1] + 1.0 / phi[1:]))])
+    fl = np.flatnonzero(~solid.reshape(-1))
+    x = fl % nx
+    F = np.zeros((fl.size, 64))
+    F[:, 0:3] = prof[:, x].T
+    F[:, 3] = x / (nx - 1)
+    for q in range(3):
+        F[:, 4 + q] = boxes[q].reshape(-1)[fl]
+    F[:, 7] = 0.5 * case.current_A_cm2
+    F[:, 8:11] = np.array(case.x_in)[None, :]
+    F[:, 11] = F[:, 3] * F[:, 7]
+    F[:, 12] = phi[x]
+    F[:, 13] = res[x] / res[-1]
+    F[:, 14] = 0.25 / phi[x]
+    F[:, 15] = 1.0
+    return F
+
+
+@pytest.mark.parametrize("gemm", GEMMS)
+def test_full_width_network_products(L, gemm):
+    """The products of the network as the warm start trains it (width 704,
+    batch 8192): forward 8192 x 704 x 64, 8192 x 704 x 704 and 8192 x 64 x 704;
+    weight gradients 704 x 704 x 8192 with the K = 8192 reduction split in 16
+    (704 = 5.5 tiles of 128 rows); input gradients.  Output, loss and every
+    gradient against the FP32 reference, element by element."""
+    net, layers = _random_net(L, 704, 2, 23)
+    net.set_gemm(gemm)
+    bits, x = _features(L, 8192, 24)
+    t = np.random.default_rng(25).standard_normal((8192, 3)).astype(np.float32)
+    out = net.forward(bits)
+    loss = net.train_batch(bits, t, lr=0.0)
+    ref_out, ref_loss, ref_grads = _reference(layers, x, t)
+    assert np.all(np.abs(out - ref_out) <= 2e-2 * np.abs(ref_out) + 1e-2 * np.abs(ref_out).max())
+    assert loss == pytest.approx(ref_loss, rel=1e-3)
+    for (gW, gb), (rW, rb) in zip(net.get(1), ref_grads):
+        for g, r in ((gW, rW), (gb, rb)):
+            assert _rel(g, r) < 3e-2
+            assert np.all(np.abs(g - r) <= 3e-2 * np.abs(r) + 2e-2 * np.abs(r).max())
+    assert _used_only(net, gemm)
+    net.close()
+
+
+@pytest.mark.parametrize("shape", [(12, 10, 30), (24, 50)])
+def test_feature_rows_match_an_independent_build(L, shape):
+    """Every entry of the GPU-built feature rows (box filters, per-x table,
+    assembly) against the numpy build above, to one BF16 rounding."""
+    case = cases.porous(shape, radius=2, porosity=0.5, seed=91, current_A_cm2=1.25,
+                        x_in=(0.6, 0.15, 0.25))
+    s = L.Solver.from_case(case, precision="fp32")
+    s.set_bc(case.x_in, case.current_A_cm2)
+    net = L.Net(width=64, depth=1, seed=3)
+    got = net.features(s, case.n_fluid)
+    ref = _reference_features(case)
+    want = L.from_bf16_bits(L.to_bf16_bits(ref.astype(np.float32))).reshape(ref.shape)
+    assert got.shape == ref.shape
+    assert np.all(np.abs(got - want) <= 2.0 ** -7 * np.abs(want) + 1e-30), \
+        np.argwhere(np.abs(got - want) > 2.0 ** -7 * np.abs(want))[:5]
+    assert np.all(got[:, 16:] == 0.0)
+    net.close()
+    s.close()
