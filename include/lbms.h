@@ -97,7 +97,22 @@ typedef struct {
  *             W-step changes of X, X += rho / (1 - rho) * (last change) when
  *             two successive ratios agree within 2 % and 0.05 < rho < 0.98).
  *             The fixed point is unchanged; only the approach is shortened.
+ *             With W > 0, a case that meets tol is not done yet: one final
+ *             extrapolation is taken at its next W-step check (from the
+ *             last two W-step changes, or from the snapshots of the current
+ *             reduced-rank cycle, see extrapolate_modes), and the case is
+ *             done when it meets tol again after it.  The residual measures
+ *             the rate of change, so the error it leaves is largest along
+ *             the slowest mode; the final extrapolation removes most of it.
  *             0 = off [0]
+ *  extrapolate_modes  how the extrapolation every W steps works: 0 or 1:
+ *             the single-mode jump above; M in 2..6: reduced-rank
+ *             extrapolation (RRE) over M + 1 snapshots of X taken W steps
+ *             apart, X = sum_j gamma_j x_j with gamma minimising
+ *             || sum_j gamma_j (x_{j+1} - x_j) || subject to sum_j gamma_j = 1
+ *             (per case, FP64), which removes up to M - 1 decay modes at once;
+ *             a case whose snapshot differences do not shrink is left alone.
+ *             Holds (M + 1) x 3 x cells doubles of snapshots [1]
  *  step_variant  0: the autotuner picks the step kernel's tile, thread
  *             mapping (a thread per cell and species, or per cell) and
  *             neighbour lookup by timing; k in 1..10 forces variant k - 1
@@ -145,6 +160,7 @@ typedef struct {
     void *(*alloc)(size_t bytes, void *stream, void *user);
     void (*free)(void *ptr, size_t bytes, void *stream, void *user);
     void *alloc_user;
+    int extrapolate_modes;
 } lbms_options;
 
 typedef struct {

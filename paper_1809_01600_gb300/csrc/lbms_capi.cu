@@ -518,6 +518,9 @@ bool bad_case(const lbms_ctx* c, int k) { return !c || k < 0 || k >= (int)c->cas
 struct Extrapolator {
     std::vector<double> norm_prev, rho_prev, coef;
     int64_t since = 0;
+    int rre_n = 0;                     // snapshots taken in the current reduced-rank cycle
+    std::vector<double> rre_coef;      // [cases][order]
+    std::vector<int> polish;           // per case: 0 not yet at tol, 1 final extrapolation pending, 2 done
 };
 
 lbms_status extrap_begin(lbms_ctx* c, Extrapolator& ex) {
@@ -530,6 +533,7 @@ lbms_status extrap_begin(lbms_ctx* c, Extrapolator& ex) {
     ex.norm_prev.assign(n, -1.0);
     ex.rho_prev.assign(n, -1.0);
     ex.coef.assign(n, 0.0);
+    ex.polish.assign(n, 0);
     ex.since = 0;
     // E = X (coefficient 0 leaves X alone)
     CK(cudaMemcpyAsync(c->L.b.coef, ex.coef.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "coef");
@@ -546,7 +550,15 @@ lbms_status extrap_check(lbms_ctx* c, Extrapolator& ex) {
         const double* o = c->host_out + (size_t)k * 10;
         const double nrm = std::sqrt(o[0] + o[1] + o[2]);
         double cf = 0.0;
-        if (ex.norm_prev[k] > 0.0 && std::isfinite(nrm)) {
+        if (ex.polish[k] == 1 && ex.norm_prev[k] > 0.0 && std::isfinite(nrm)) {
+            // the final extrapolation of a case that met tol: by now the slowest
+            // mode dominates both W-step changes, so one ratio suffices
+            const double rho = nrm / ex.norm_prev[k];
+            if (rho > 0.05 && rho < 0.98) cf = rho / (1.0 - rho);
+            ex.polish[k] = 2;
+            ex.norm_prev[k] = -1.0;
+            ex.rho_prev[k] = -1.0;
+        } else if (ex.norm_prev[k] > 0.0 && std::isfinite(nrm)) {
             const double rho = nrm / ex.norm_prev[k];
             if (ex.rho_prev[k] > 0.0 && std::fabs(rho - ex.rho_prev[k]) <= 0.02 * rho && rho > 0.05 && rho < 0.98) {
                 cf = rho / (1.0 - rho);
@@ -565,6 +577,136 @@ lbms_status extrap_check(lbms_ctx* c, Extrapolator& ex) {
     c->h2d += n * sizeof(double);
     CK(launch_extrapolate(c->L, c->stream), "extrapolation kernel");
     ex.since = 0;
+    return LBMS_OK;
+}
+
+// Reduced-rank extrapolation (extrapolate_modes = M >= 2): every W steps a
+// snapshot of X; after M + 1 snapshots x_0 .. x_M (differences u_a = x_{a+1}
+// - x_a), per case the coefficients gamma minimising || sum_j gamma_j u_j ||
+// with sum_j gamma_j = 1 (normal equations G y = 1 with a relative ridge of
+// 1e-12, gamma = y / sum y), and X += sum_a c_a u_a with c_a = -sum_{j<=a}
+// gamma_j, i.e. X = sum_j gamma_j x_j.  A case is left alone (c = 0) when its
+// differences do not shrink (u_{M-1} no smaller than u_0: not yet in the
+// contracting regime), when the solve is not finite, or when the step would
+// exceed 500 times the last difference.  The new X is the first snapshot of
+// the next cycle.
+bool rre_solve(int m, const double* packed, double* c) {
+    double G[kRreMaxOrder][kRreMaxOrder];
+    int v = 0;
+    for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b) G[a][b] = G[b][a] = packed[v++];
+    for (int a = 0; a < m; ++a) c[a] = 0.0;
+    double tr = 0.0;
+    for (int a = 0; a < m; ++a) tr += G[a][a];
+    if (!(tr > 0.0) || !std::isfinite(tr)) return false;
+    if (!(G[m - 1][m - 1] < G[0][0])) return false;
+    double A[kRreMaxOrder][kRreMaxOrder];
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) A[a][b] = G[a][b] / tr + (a == b ? 1e-12 : 0.0);
+    // Cholesky A = R^T R, then R^T R y = 1
+    double R[kRreMaxOrder][kRreMaxOrder] = {};
+    for (int i = 0; i < m; ++i) {
+        for (int j = i; j < m; ++j) {
+            double sum = A[i][j];
+            for (int k = 0; k < i; ++k) sum -= R[k][i] * R[k][j];
+            if (i == j) {
+                if (!(sum > 0.0)) return false;
+                R[i][i] = std::sqrt(sum);
+            } else {
+                R[i][j] = sum / R[i][i];
+            }
+        }
+    }
+    double y[kRreMaxOrder];
+    for (int i = 0; i < m; ++i) {
+        double sum = 1.0;
+        for (int k = 0; k < i; ++k) sum -= R[k][i] * y[k];
+        y[i] = sum / R[i][i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        double sum = y[i];
+        for (int k = i + 1; k < m; ++k) sum -= R[i][k] * y[k];
+        y[i] = sum / R[i][i];
+    }
+    double sy = 0.0;
+    for (int i = 0; i < m; ++i) sy += y[i];
+    if (!(std::fabs(sy) > 0.0) || !std::isfinite(sy)) return false;
+    double run = 0.0;
+    for (int a = 0; a < m; ++a) {
+        run += y[a] / sy;
+        c[a] = -run;
+    }
+    // predicted step norm^2 = c^T G c
+    double step = 0.0;
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) step += c[a] * G[a][b] * c[b];
+    if (!std::isfinite(step) || step > 500.0 * 500.0 * G[m - 1][m - 1]) {
+        for (int a = 0; a < m; ++a) c[a] = 0.0;
+        return false;
+    }
+    return true;
+}
+
+lbms_status rre_begin(lbms_ctx* c, Extrapolator& ex) {
+    Launch& L = c->L;
+    const int m = c->opt.extrapolate_modes;
+    const int nv = m * (m + 1) / 2;
+    if (!L.b.rre_ring) {
+        // sized for the order of this handle's option (fixed at create)
+        L.b.rre_ring = static_cast<double*>(dev_alloc(c, (size_t)(m + 1) * 3 * L.S * sizeof(double)));
+        L.b.rre_partials = static_cast<double*>(dev_alloc(c, (size_t)L.n_segs * nv * sizeof(double)));
+        L.b.rre_out = static_cast<double*>(dev_alloc(c, (size_t)L.n_cases * nv * sizeof(double)));
+        L.b.rre_coef = static_cast<double*>(dev_alloc(c, (size_t)L.n_cases * m * sizeof(double)));
+        if (!L.b.rre_ring || !L.b.rre_partials || !L.b.rre_out || !L.b.rre_coef)
+            return fail(c, LBMS_ENOMEM, "reduced-rank extrapolation buffers");
+    }
+    ex.rre_coef.assign((size_t)L.n_cases * m, 0.0);
+    ex.coef.assign(L.n_cases, 0.0);
+    ex.polish.assign(L.n_cases, 0);
+    ex.since = 0;
+    CK(launch_rre_snapshot(L, 0, c->stream), "extrapolation snapshot");
+    ex.rre_n = 1;
+    return LBMS_OK;
+}
+
+// One snapshot; at the end of a cycle the extrapolation.  ex.coef[k] != 0
+// marks the cases that moved.
+lbms_status rre_check(lbms_ctx* c, Extrapolator& ex) {
+    Launch& L = c->L;
+    const int m = c->opt.extrapolate_modes;
+    const int nv = m * (m + 1) / 2;
+    const int n = L.n_cases;
+    ex.since = 0;
+    for (int k = 0; k < n; ++k) ex.coef[k] = 0.0;
+    CK(launch_rre_snapshot(L, ex.rre_n, c->stream), "extrapolation snapshot");
+    ++ex.rre_n;
+    // a full cycle, or an early one (at least two differences) for the
+    // final extrapolation of cases that met tol; an early cycle moves only
+    // those cases
+    bool pending = false;
+    for (int k = 0; k < n; ++k) pending = pending || ex.polish[k] == 1;
+    const bool full_cycle = ex.rre_n > m;
+    if (!full_cycle && !(pending && ex.rre_n >= 3)) return LBMS_OK;
+    const int mm = full_cycle ? m : ex.rre_n - 1;
+    const int nvv = mm * (mm + 1) / 2;
+    CK(launch_rre_gram(L, mm, c->stream), "extrapolation Gram matrices");
+    std::vector<double> gram((size_t)n * nvv);
+    CK(cudaMemcpyAsync(gram.data(), L.b.rre_out, gram.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "Gram readback");
+    CK(cudaStreamSynchronize(c->stream), "Gram readback");
+    c->d2h += gram.size() * sizeof(double);
+    ex.rre_coef.assign((size_t)n * mm, 0.0);
+    for (int k = 0; k < n; ++k) {
+        if (!full_cycle && ex.polish[k] != 1) continue;
+        if (rre_solve(mm, gram.data() + (size_t)k * nvv, ex.rre_coef.data() + (size_t)k * mm)) ex.coef[k] = 1.0;
+        if (ex.polish[k] == 1) ex.polish[k] = 2;
+    }
+    CK(cudaMemcpyAsync(L.b.rre_coef, ex.rre_coef.data(), ex.rre_coef.size() * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream),
+       "extrapolation coefficients");
+    c->h2d += ex.rre_coef.size() * sizeof(double);
+    CK(launch_rre_apply(L, mm, c->stream), "extrapolation kernel");
+    ex.rre_n = 1;
     return LBMS_OK;
 }
 
@@ -608,6 +750,7 @@ void lbms_default_options(lbms_options* o) {
     o->tau_max = 5.0;
     o->dt_s = 0.0;
     o->check_every = 100;
+    o->extrapolate_modes = 1;
 }
 
 const char* lbms_status_string(lbms_status s) {
@@ -647,6 +790,8 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         lbms_default_options(&c->opt);
     if (c->opt.check_every <= 0) c->opt.check_every = 100;
     if (c->opt.extrapolate_every < 0) c->opt.extrapolate_every = 0;
+    if (c->opt.extrapolate_modes < 0 || c->opt.extrapolate_modes > kRreMaxOrder)
+        return bail(fail(c, LBMS_EINVAL, "extrapolate_modes must be in 0..%d", kRreMaxOrder));
     if (c->opt.step_variant < 0 || c->opt.step_variant > kStepVariants) return bail(fail(c, LBMS_EINVAL, "step_variant out of range"));
     if (c->opt.init_mode != LBMS_INIT_UNIFORM && c->opt.init_mode != LBMS_INIT_PROFILE_1D)
         return bail(fail(c, LBMS_EINVAL, "init_mode must be LBMS_INIT_UNIFORM or LBMS_INIT_PROFILE_1D"));
@@ -1030,8 +1175,9 @@ lbms_status lbms_batch_run_to_residual(lbms_ctx* c, double tol, int64_t max_step
     CK(launch_case_residuals(c->L, 1, c->stream), "residual kernels");  // snapshots start here
     lbms_status st = LBMS_OK;
     const int64_t W = c->opt.extrapolate_every;
+    const bool rre = c->opt.extrapolate_modes >= 2;
     Extrapolator ex;
-    if (W > 0) st = extrap_begin(c, ex);
+    if (W > 0) st = rre ? rre_begin(c, ex) : extrap_begin(c, ex);
     bool all = false;
     while (st == LBMS_OK && done < max_steps && !all) {
         const int64_t k = std::min<int64_t>(K, max_steps - done);
@@ -1041,7 +1187,7 @@ lbms_status lbms_batch_run_to_residual(lbms_ctx* c, double tol, int64_t max_step
         st = case_residuals(c, (int)k, r.data());
         if (st != LBMS_OK) break;
         if (W > 0 && (ex.since += k) >= W) {
-            st = extrap_check(c, ex);
+            st = rre ? rre_check(c, ex) : extrap_check(c, ex);
             if (st != LBMS_OK) break;
             // a jump is never the last thing before a convergence decision:
             // the next residual check sees it in its K-step change
@@ -1051,7 +1197,14 @@ lbms_status lbms_batch_run_to_residual(lbms_ctx* c, double tol, int64_t max_step
         }
         all = true;
         for (int q = 0; q < n; ++q) {
-            if (met[q] < 0 && r[q] <= tol) met[q] = done;
+            if (met[q] < 0 && r[q] <= tol) {
+                // with extrapolation a case is done when it meets tol again
+                // after one final extrapolation taken at its next W-step check
+                if (W > 0 && ex.polish[q] == 0)
+                    ex.polish[q] = 1;
+                else if (W <= 0 || ex.polish[q] == 2)
+                    met[q] = done;
+            }
             all = all && met[q] >= 0;
         }
     }

@@ -149,6 +149,62 @@ cudaError_t launch_extrapolate(const Launch& L, cudaStream_t st) {
     return L.precision == 0 ? extrapolate_t<double>(L, st) : extrapolate_t<float>(L, st);
 }
 
+cudaError_t launch_rre_snapshot(const Launch& L, int slot, cudaStream_t st) {
+    if (L.precision == 0)
+        seg_snapshot_kernel<double><<<L.n_segs, kSegThreads, 0, st>>>(static_cast<const double*>(L.b.X[L.cur]),
+                                                                      L.b.rre_ring, L.S, L.b.segs, slot);
+    else
+        seg_snapshot_kernel<float><<<L.n_segs, kSegThreads, 0, st>>>(static_cast<const float*>(L.b.X[L.cur]),
+                                                                     L.b.rre_ring, L.S, L.b.segs, slot);
+    return cudaGetLastError();
+}
+
+namespace {
+template <int M>
+cudaError_t rre_gram_m(const Launch& L, cudaStream_t st) {
+    constexpr int NV = M * (M + 1) / 2;
+    seg_gram_kernel<M><<<L.n_segs, kSegThreads, 0, st>>>(L.b.rre_ring, L.S, L.b.segs, L.b.rre_partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    seg_finalize_kernel<NV><<<L.n_cases, kSegThreads, 0, st>>>(L.b.rre_partials, L.b.case_segs, L.b.rre_out);
+    return cudaGetLastError();
+}
+template <int M>
+cudaError_t rre_apply_m(const Launch& L, cudaStream_t st) {
+    if (L.precision == 0)
+        seg_rre_apply_kernel<double, M><<<L.n_segs, kSegThreads, 0, st>>>(
+            static_cast<double*>(L.b.X[L.cur]), static_cast<double*>(L.b.X[L.cur ^ 1]), L.b.rre_ring, L.S, L.b.segs,
+            L.b.seg_case, L.b.rre_coef);
+    else
+        seg_rre_apply_kernel<float, M><<<L.n_segs, kSegThreads, 0, st>>>(
+            static_cast<float*>(L.b.X[L.cur]), static_cast<float*>(L.b.X[L.cur ^ 1]), L.b.rre_ring, L.S, L.b.segs,
+            L.b.seg_case, L.b.rre_coef);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_rre_gram(const Launch& L, int order, cudaStream_t st) {
+    switch (order) {
+        case 2: return rre_gram_m<2>(L, st);
+        case 3: return rre_gram_m<3>(L, st);
+        case 4: return rre_gram_m<4>(L, st);
+        case 5: return rre_gram_m<5>(L, st);
+        case 6: return rre_gram_m<6>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_rre_apply(const Launch& L, int order, cudaStream_t st) {
+    switch (order) {
+        case 2: return rre_apply_m<2>(L, st);
+        case 3: return rre_apply_m<3>(L, st);
+        case 4: return rre_apply_m<4>(L, st);
+        case 5: return rre_apply_m<5>(L, st);
+        case 6: return rre_apply_m<6>(L, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t launch_case_residuals(const Launch& L, int update, cudaStream_t st) {
     return L.precision == 0 ? residual_t<double>(L, update, st) : residual_t<float>(L, update, st);
 }

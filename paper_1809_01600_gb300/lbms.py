@@ -36,7 +36,8 @@ EXPORTS = ("lbms_default_options", "lbms_create", "lbms_set_bc", "lbms_set_field
            "lbms_last_error", "lbms_status_string", "lbms_residual_sums_noalloc",
            "lbms_create_batch", "lbms_batch_set_bc", "lbms_batch_set_fields", "lbms_batch_residuals",
            "lbms_batch_run_to_residual", "lbms_batch_get_fields", "lbms_batch_overpotentials")
-NET_EXPORTS = ("lbms_net_create", "lbms_net_add_sample", "lbms_net_train", "lbms_net_warm_start",
+NET_EXPORTS = ("lbms_net_create", "lbms_net_add_sample", "lbms_net_features", "lbms_net_train",
+               "lbms_net_warm_start", "lbms_net_set_gemm", "lbms_net_gemm_calls",
                "lbms_net_forward", "lbms_net_train_batch", "lbms_net_get", "lbms_net_set", "lbms_net_info",
                "lbms_net_last_error", "lbms_net_destroy")
 
@@ -74,7 +75,7 @@ class Options(C.Structure):
                 ("extrapolate_every", C.c_int), ("step_variant", C.c_int),
                 ("init_mode", C.c_int), ("outlet_bc", C.c_int), ("grad_stencil", C.c_int),
                 ("stream", C.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", C.c_void_p)]
+                ("alloc_user", C.c_void_p), ("extrapolate_modes", C.c_int)]
 
 
 class Info(C.Structure):
@@ -133,6 +134,9 @@ def load(build_if_needed: bool = True):
         "lbms_batch_overpotentials": (st, [P, D, D]),
         "lbms_net_create": (st, [C.c_int, C.c_int, C.c_uint64, C.POINTER(P)]),
         "lbms_net_add_sample": (st, [P, P, C.c_int]),
+        "lbms_net_features": (st, [P, P, C.c_int, P, I64]),
+        "lbms_net_set_gemm": (st, [P, C.c_int]),
+        "lbms_net_gemm_calls": (st, [P, C.POINTER(I64), C.POINTER(I64)]),
         "lbms_net_train": (st, [P, C.c_int, C.c_int, C.c_double, D]),
         "lbms_net_warm_start": (st, [P, P, C.c_int, D]),
         "lbms_net_forward": (st, [P, P, C.c_int, P]),
@@ -161,7 +165,7 @@ class _Handle:
     def _setup(self, molar_mass, fuller_volume, stoich, electrons, D_binary, pore_diameter,
                eps_over_tau, precision, coupling, tau_min, tau_max, dt, check_every, stream,
                torch_allocator, extrapolate_every=0, step_variant=0, init_mode="uniform",
-               outlet_bc="flux", grad_stencil="central"):
+               outlet_bc="flux", grad_stencil="central", extrapolate_modes=1):
         lib = load()
         self._lib = lib
         self._mm = np.ascontiguousarray(molar_mass, dtype=np.float64)
@@ -184,6 +188,7 @@ class _Handle:
         o.dt_s = float(dt or 0.0)
         o.check_every = int(check_every)
         o.extrapolate_every = int(extrapolate_every)
+        o.extrapolate_modes = int(extrapolate_modes)
         o.step_variant = int(step_variant)
         o.init_mode = _INIT_MODES[init_mode]
         o.outlet_bc = _OUTLETS[outlet_bc]
@@ -281,13 +286,15 @@ class Batch(_Handle):
     def __init__(self, solids, dim=None, length_x=2e-3, periodic_x=False, *, T=1073.0, p=101325.0,
                  precision="fp32", coupling="ms", tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100,
                  stream=None, torch_allocator=True, extrapolate_every=0, step_variant=0,
-                 init_mode="uniform", outlet_bc="flux", grad_stencil="central", **gas):
+                 init_mode="uniform", outlet_bc="flux", grad_stencil="central", extrapolate_modes=1,
+                 **gas):
         g = dict(_GAS_DEFAULTS)
         g.update(gas)
         sp, df, o = self._setup(g["molar_mass"], g["fuller_volume"], g["stoich"], g["electrons"],
                                 g["D_binary"], g["pore_diameter"], g["eps_over_tau"], precision,
                                 coupling, tau_min, tau_max, dt, check_every, stream, torch_allocator,
-                                extrapolate_every, step_variant, init_mode, outlet_bc, grad_stencil)
+                                extrapolate_every, step_variant, init_mode, outlet_bc, grad_stencil,
+                                extrapolate_modes)
         n = len(solids)
         lx = list(length_x) if np.ndim(length_x) else [length_x] * n
         px = list(periodic_x) if np.ndim(periodic_x) else [periodic_x] * n
@@ -375,11 +382,11 @@ class Solver(_Handle):
                  eps_over_tau=1.0, T=1073.0, p=101325.0, precision="fp32", coupling="ms",
                  tau_min=1.0, tau_max=5.0, dt=0.0, check_every=100, stream=None,
                  torch_allocator=True, extrapolate_every=0, step_variant=0, init_mode="uniform",
-                 outlet_bc="flux", grad_stencil="central"):
+                 outlet_bc="flux", grad_stencil="central", extrapolate_modes=1):
         sp, df, o = self._setup(molar_mass, fuller_volume, stoich, electrons, D_binary,
                                 pore_diameter, eps_over_tau, precision, coupling, tau_min, tau_max,
                                 dt, check_every, stream, torch_allocator, extrapolate_every,
-                                step_variant, init_mode, outlet_bc, grad_stencil)
+                                step_variant, init_mode, outlet_bc, grad_stencil, extrapolate_modes)
         g, mask, shape, dim = self._geometry(solid, dim, length_x, periodic_x)
         self._mask = mask
         self.shape = shape
@@ -490,6 +497,24 @@ class Net:
 
     def add_sample(self, handle, case=0):
         self._check(self._lib.lbms_net_add_sample(self._h, handle._h, int(case)))
+
+    GEMM_KINDS = {"auto": 0, "tcgen05": 1, "mma_sync": 2}
+
+    def set_gemm(self, kind):
+        """Which kernel computes the matrix products: auto, tcgen05, mma_sync."""
+        self._check(self._lib.lbms_net_set_gemm(self._h, self.GEMM_KINDS[kind]))
+
+    def gemm_calls(self):
+        """(tcgen05 products, mma.sync products) computed so far."""
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self._lib.lbms_net_gemm_calls(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def features(self, handle, n_fluid, case=0):
+        """The case's feature rows as float32 [n_fluid, FEATURES] (from BF16)."""
+        bits = np.empty((int(n_fluid), self.FEATURES), dtype=np.uint16)
+        self._check(self._lib.lbms_net_features(self._h, handle._h, int(case), bits.ctypes.data, int(n_fluid)))
+        return from_bf16_bits(bits).reshape(int(n_fluid), self.FEATURES)
 
     def train(self, iters, batch=8192, lr=1e-3):
         loss = C.c_double()
