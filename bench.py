@@ -33,6 +33,7 @@ WORKLOADS = {
     "anode3d_256x128x128": "anode_3d_256x128x128",
     "anode2d_96x48": "anode_2d_96x48",
     "anode3d_512": "anode_3d_512",
+    "anode3d_small": "anode_3d_small",
     "sweep": None,
     "table2": None,
     "warmstart": None,
@@ -49,24 +50,47 @@ def parse():
     ap.add_argument("--workload", default="anode3d_256x128x128", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "fp16"])
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp16-line", action="store_true",
+                    help="skip the throughput of the 16-bit storage form in the FP32 line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--time-to-residual", type=float, default=0.0,
-                    help="also run to this residual from the uniform start and report the time")
-    ap.add_argument("--ttr-forms", default="",
-                    help="comma list of time-to-residual forms to run: plain_fp32, plain_fp64, "
+    ap.add_argument("--time-to-residual", type=float, default=1e-8,
+                    help="run each time-to-residual form to this residual and report the time "
+                         "(the second half of the metric); 0 or --no-ttr skips it")
+    ap.add_argument("--no-ttr", action="store_true", help="skip the time-to-residual forms")
+    ap.add_argument("--ttr-forms", default="plain_fp32,fp16_extrapolated_network",
+                    help="comma list of time-to-residual forms: plain_fp32, plain_fp64, "
                          "fp16_extrapolated, fp32_extrapolated, fp16_extrapolated_profile1d, "
-                         "fp16_extrapolated_network (default: plain_fp32 and the three "
-                         "extrapolated forms without the network)")
+                         "fp16_extrapolated_network (the chosen form: network start, FP16 "
+                         "storage, extrapolation)")
+    ap.add_argument("--no-ttr-reference", action="store_true",
+                    help="skip the overpotential reference (FP32 run on to its floor, FP64 polish)")
+    ap.add_argument("--ref-tol", type=float, default=3e-10,
+                    help="residual the FP32 leg of the overpotential reference runs to")
+    ap.add_argument("--ref-fp64-steps", type=int, default=20000,
+                    help="FP64 steps that polish the overpotential reference")
+    ap.add_argument("--oracle-procs", type=int, default=0,
+                    help="oracle processes for the CPU baseline (0: one per host core)")
+    ap.add_argument("--oracle-ttr", action="store_true",
+                    help="--impl reference: also run the oracle to the residual on the workload")
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--step-variant", type=int, default=0,
                     help="0: the autotuner picks the step kernel; k > 0 forces variant k - 1 "
                          "(to profile the variant a plain run picked)")
     ap.add_argument("--extrapolate-every", type=int, default=20000,
                     help="W of the slowest-mode extrapolation in the accelerated time-to-residual run")
-    ap.add_argument("--sweep-2d", type=int, default=8, help="2-D microstructures of the sweep")
-    ap.add_argument("--sweep-3d", type=int, default=8, help="3-D microstructures of the sweep")
+    ap.add_argument("--rre-every", type=int, default=10000,
+                    help="W of the reduced-rank extrapolation forms (snapshots W steps apart)")
+    ap.add_argument("--rre-modes", type=int, default=4,
+                    help="order M of the reduced-rank extrapolation forms (M + 1 snapshots)")
+    ap.add_argument("--ttr-chosen", default="fp16_extrapolated_network",
+                    help="the form reported as the chosen one (its end state seeds the reference)")
+    ap.add_argument("--sweep-2d", type=int, default=32, help="2-D microstructures of the sweep")
+    ap.add_argument("--sweep-3d", type=int, default=32, help="3-D microstructures of the sweep")
     ap.add_argument("--sweep-scale", type=float, default=1.0, help="size factor of the sweep grids")
     ap.add_argument("--sweep-points", type=int, default=8, help="operating points per microstructure")
+    ap.add_argument("--sweep-small-scale", type=float, default=0.25,
+                    help="size factor of the small-case sweep timed batched against one handle per case "
+                         "(0 skips it)")
     ap.add_argument("--ws-train", type=int, default=128, help="warm start: training anodes")
     ap.add_argument("--ws-test", type=int, default=16, help="warm start: held-out anodes")
     ap.add_argument("--ws-iters", type=int, default=6000, help="warm start: Adam steps")
@@ -210,23 +234,6 @@ def ncu_traffic(workload, precision, variant):
 
 
 # ------------------------------------------------------------- oracle
-def oracle_sample(case, budget_s, steps_hint):
-    """A z-slab of the workload (periodic), sized so one oracle step takes
-    about budget_s / steps_hint seconds."""
-    from oracle import Oracle
-    nz = case.solid.shape[0]
-    slab = max(1, min(nz, 2))
-    probe = case.with_(solid=np.ascontiguousarray(case.solid[:slab]))
-    o = Oracle(probe)
-    t = time.perf_counter()
-    o.step(1)
-    per = time.perf_counter() - t
-    per_plane = per / slab
-    target = budget_s / max(1, steps_hint)
-    planes = int(max(1, min(nz, target / max(per_plane, 1e-9))))
-    return case.with_(solid=np.ascontiguousarray(case.solid[:planes])), planes
-
-
 def run_oracle(case, steps, warmup):
     from oracle import Oracle
     o = Oracle(case)
@@ -236,9 +243,193 @@ def run_oracle(case, steps, warmup):
     return time.perf_counter() - t
 
 
+def _oracle_slab(workload, z0, z1, steps, warmup, barrier, queue):
+    """One oracle process: z-planes [z0, z1) of the workload's mask (periodic
+    in z), `warmup` untimed steps, then `steps` timed ones between wall-clock
+    stamps taken after every process has warmed up."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import Oracle
+    case = make_case(workload)
+    sub = case.with_(solid=np.ascontiguousarray(case.solid[z0:z1]))
+    o = Oracle(sub)
+    o.step(warmup)
+    barrier.wait()
+    t0 = time.time()
+    o.step(steps)
+    queue.put((sub.n_fluid, t0, time.time()))
+
+
+def oracle_all_cores(workload, steps, warmup, procs=0, planes=0):
+    """The FP64 oracle on every host core: the first `planes` z-planes of the
+    workload (0: all) split into one slab per process (each slab periodic in
+    z), run concurrently; returns (fluid cells, wall seconds of the timed
+    steps, processes, planes)."""
+    import multiprocessing as mp
+    case = make_case(workload)
+    nz = planes or case.solid.shape[0]
+    procs = max(1, min(procs or os.cpu_count() or 1, nz))
+    bounds = [(k * nz // procs, (k + 1) * nz // procs) for k in range(procs)]
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    queue = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_slab, args=(workload, z0, z1, steps, warmup, barrier, queue))
+          for z0, z1 in bounds]
+    for p in ps:
+        p.start()
+    res = [queue.get() for _ in ps]
+    for p in ps:
+        p.join()
+    cells = sum(r[0] for r in res)
+    wall = max(r[2] for r in res) - min(r[1] for r in res)
+    return cells, wall, procs, nz
+
+
 def cores_used():
-    # numpy element-wise kernels run on one thread
+    # numpy element-wise kernels run on one thread per process
     return 1
+
+
+# ------------------------------------------------------- throughput / ttr
+def time_steps(L, case, precision, args, dist):
+    """Throughput of one more handle of the workload at `precision`: the
+    same warm-up and CUDA-event timing as the main line, with its roofline
+    on the algorithmic bytes of that precision."""
+    import torch
+    s = L.Solver.from_case(case, precision=precision)
+    s.set_bc(case.x_in, case.current_A_cm2)
+    info = s.info()
+    s.step(args.warmup)
+    s.step(32)
+    s.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    s.close()
+    t_dev = max_over_ranks(dist, ms / 1e3, "cuda")
+    nf = case.n_fluid
+    bpc = bytes_per_cell(case.dim, precision)
+    achieved = nf * bpc / (t_dev / args.steps) / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    return {"precision": precision, "ms_per_step": round(ms / args.steps, 5),
+            "value": round(nf * 3 * args.steps * (dist.get_world_size() if dist else 1) / t_dev / 1e6, 2),
+            "unit": METRIC, "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                         "bytes_per_fluid_cell": bpc, "variant": variant_key(info),
+                         "traffic": ncu_traffic(case.name, precision, variant_key(info))}}
+
+
+def _run_form(L, case, label, prec, W, init, tol, args, net=None, X0=None, modes=1):
+    """One time-to-residual run on a fresh handle, timed from its boundary
+    data being set (the network's prediction, when it starts from one, is
+    inside the time) to the residual check that meets tol; clocks sampled
+    over the run."""
+    import torch
+    s = L.Solver.from_case(case, precision=prec, extrapolate_every=W, extrapolate_modes=modes,
+                           init_mode="profile1d" if init == "profile1d" else "uniform")
+    s.set_bc(case.x_in, case.current_A_cm2)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    t = time.perf_counter()
+    if init == "network":
+        net.warm_start(s)
+    elif X0 is not None:
+        s.set_fields(X0)
+    n, r, st = s.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t
+    clk = clocks.stop()
+    eta, xo = s.overpotential()
+    info = s.info()
+    out = {"precision": prec, "extrapolate_every": W, "extrapolate_modes": modes, "init": init,
+           "steps": int(n), "residual": r,
+           "seconds": round(secs, 3), "converged": st == L.LBMS_OK, "eta_V": eta,
+           "variant": variant_key(info), "clocks": clk}
+    return s, out
+
+
+def time_to_residual(L, case, args):
+    """Time to residual tol from the start of each form, plain FP32 against
+    the chosen form (network start + FP16 storage + extrapolation), and the
+    overpotential of each against a reference steady state: the chosen
+    form's end state run on in FP32 with extrapolation to its floor
+    (residual --ref-tol), then --ref-fp64-steps FP64 steps."""
+    tol = args.time_to_residual
+    Wx, Wr, M = args.extrapolate_every, args.rre_every, args.rre_modes
+    forms = {"plain_fp32": ("fp32", 0, "uniform", 1),
+             "plain_fp64": ("fp64", 0, "uniform", 1),
+             "fp16_extrapolated": ("fp16", Wx, "uniform", 1),
+             "fp32_extrapolated": ("fp32", Wx, "uniform", 1),
+             "fp16_extrapolated_profile1d": ("fp16", Wx, "profile1d", 1),
+             "fp16_extrapolated_network": ("fp16", Wx, "network", 1),
+             "fp32_rre": ("fp32", Wr, "uniform", M),
+             "fp16_rre": ("fp16", Wr, "uniform", M),
+             "fp16_rre_network": ("fp16", Wr, "network", M)}
+    pick = [f for f in args.ttr_forms.split(",") if f]
+    for f in pick:
+        if f not in forms:
+            raise SystemExit(f"unknown time-to-residual form {f}")
+    chosen = args.ttr_chosen if args.ttr_chosen in pick else pick[-1]
+    out = {"tol": tol, "chosen": chosen, "baseline": "plain_fp32"}
+    net = None
+    if any(forms[f][2] == "network" for f in pick):
+        from workloads import cases as W_
+        net, info = train_warmstart_net(L, W_.warmstart_cases(args.ws_train, 1000), 1e-8, args)
+        out["network"] = dict(info, note="trained on 64x32x32 anodes, none of them this one; the "
+                                         "training is outside the form's seconds, the prediction inside")
+    start = None      # end state of the chosen form: where the reference starts
+    for label in pick:
+        prec, W, init, modes = forms[label]
+        s, res = _run_form(L, case, label, prec, W, init, tol, args, net=net, modes=modes)
+        out[label] = res
+        if label == chosen:
+            start = s.fields()
+        s.close()
+    if net is not None:
+        net.close()
+    base = out.get("plain_fp32")
+    for label in pick:
+        if base and label != "plain_fp32":
+            out[label]["speedup_vs_plain_fp32"] = round(base["seconds"] / out[label]["seconds"], 2)
+    # overpotential reference: continue from the last form's state
+    if not args.no_ttr_reference and start is not None:
+        ref32, r32 = _run_form(L, case, "reference_fp32", "fp32", Wr, "uniform", args.ref_tol, args,
+                               X0=start, modes=M)
+        X = ref32.fields()
+        ref32.close()
+        import torch
+        s64 = L.Solver.from_case(case, precision="fp64")
+        s64.set_bc(case.x_in, case.current_A_cm2)
+        s64.set_fields(X)
+        t = time.perf_counter()
+        s64.step(args.ref_fp64_steps)
+        r64 = s64.residual(args.ref_fp64_steps)
+        eta64, _ = s64.overpotential()
+        torch.cuda.synchronize()
+        secs64 = time.perf_counter() - t
+        s64.close()
+        ref = {"fp32_leg": r32, "fp64_leg": {"steps": args.ref_fp64_steps, "residual": r64,
+                                               "eta_V": eta64, "seconds": round(secs64, 2)},
+               "eta_V": eta64,
+               "what": "the chosen form's end state run on in FP32 with extrapolation to residual "
+                       f"{args.ref_tol:g}, then {args.ref_fp64_steps} FP64 steps from that field"}
+        out["reference"] = ref
+        for label in pick:
+            e = out[label]["eta_V"]
+            rel = abs(e - eta64) / abs(eta64)
+            out[label]["eta_rel_err_vs_reference"] = rel
+            out[label]["eta_within_1e-4"] = bool(rel <= 1e-4)
+    return out
 
 
 # ------------------------------------------------------------------ main
@@ -294,6 +485,7 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    s.close()
     t_dev = ms / 1e3
     t_dev = max_over_ranks(dist, t_dev, "cuda")
     units = nf * 3 * args.steps * ws
@@ -315,48 +507,18 @@ def main():
                     "double" if args.precision == "fp64" else "float pair",
                     {"fp64": "double", "fp32": "float", "fp16": "__half"}[args.precision])}
 
-    # time to residual from the uniform start (optional): plain FP32 against
-    # the chosen form (FP16 storage + slowest-mode extrapolation)
+    # the same throughput with 16-bit population storage (the chosen form's
+    # storage), one more handle and the same timing
+    fp16 = None
+    if args.precision == "fp32" and not args.no_fp16_line:
+        fp16 = time_steps(L, case, "fp16", args, dist)
+
+    # time to residual 1e-8 (the second half of the metric): plain FP32
+    # against the chosen form, each with its clock record, and their
+    # overpotentials against a reference steady state
     ttr = None
-    if args.time_to_residual > 0:
-        ttr = {"tol": args.time_to_residual}
-        forms = (("plain_fp32", "fp32", 0, "uniform"),
-                 ("plain_fp64", "fp64", 0, "uniform"),
-                 ("fp16_extrapolated", "fp16", args.extrapolate_every, "uniform"),
-                 ("fp32_extrapolated", "fp32", args.extrapolate_every, "uniform"),
-                 ("fp16_extrapolated_profile1d", "fp16", args.extrapolate_every, "profile1d"),
-                 ("fp16_extrapolated_network", "fp16", args.extrapolate_every, "network"))
-        pick = (args.ttr_forms.split(",") if args.ttr_forms
-                else [f[0] for f in forms if f[0] not in ("plain_fp64", "fp16_extrapolated_network")])
-        net = None
-        if "fp16_extrapolated_network" in pick:
-            from workloads import cases as W_
-            net, info = train_warmstart_net(L, W_.warmstart_cases(args.ws_train, 1000), 1e-8, args)
-            ttr["network"] = dict(info, note="trained on 64x32x32 anodes; the prediction time is inside "
-                                             "the form's seconds, the training is not")
-        for label, prec, W, init in forms:
-            if label not in pick:
-                continue
-            r0 = L.Solver.from_case(case, precision=prec, extrapolate_every=W,
-                                    init_mode="uniform" if init == "network" else init)
-            r0.set_bc(case.x_in, case.current_A_cm2)
-            torch.cuda.synchronize()
-            t = time.perf_counter()
-            if init == "network":
-                net.warm_start(r0)
-            n, r, st = r0.run_to_residual(args.time_to_residual, args.max_steps, raise_on_fail=False)
-            ttr_s = time.perf_counter() - t
-            eta, _ = r0.overpotential()
-            ttr[label] = {"precision": prec, "extrapolate_every": W, "init": init, "steps": n, "residual": r,
-                          "seconds": round(ttr_s, 3), "converged": st == L.LBMS_OK, "eta_V": eta}
-            r0.close()
-        if net is not None:
-            net.close()
-        base = ttr.get("plain_fp32")
-        for label, _, _, _ in forms[1:]:
-            if base and label in ttr:
-                ttr[label]["speedup_vs_plain_fp32"] = round(base["seconds"] / ttr[label]["seconds"], 2)
-                ttr[label]["eta_rel_diff_vs_plain_fp32"] = abs(ttr[label]["eta_V"] - base["eta_V"]) / abs(base["eta_V"])
+    if args.time_to_residual > 0 and not args.no_ttr:
+        ttr = time_to_residual(L, case, args)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -381,12 +543,13 @@ def main():
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        sample, planes = oracle_sample(case, 20.0, 2)
-        t_cpu = run_oracle(sample, 2, 0)
-        cpu = {"value": round(sample.n_fluid * 3 * 2 / t_cpu / 1e6, 4), "unit": METRIC,
-               "cores": cores_used(), "kind": "oracle",
-               "sample": f"2 FP64 oracle steps on the first {planes} z-planes of the same "
-                         f"{case.name} mask ({sample.n_fluid} fluid cells, periodic in z)"}
+        csteps = 10
+        cells, wall, procs, planes = oracle_all_cores(args.workload, csteps, 1, args.oracle_procs)
+        cpu = {"value": round(cells * 3 * csteps / wall / 1e6, 4), "unit": METRIC,
+               "cores": procs * cores_used(), "kind": "oracle",
+               "sample": f"{csteps} timed FP64 oracle steps (after 1 untimed) on all {planes} z-planes of "
+                         f"the same {case.name} mask, split into {procs} z-slabs (each periodic in z) run "
+                         f"concurrently by {procs} single-threaded processes ({cells} fluid cells)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": ws,
@@ -401,22 +564,24 @@ def main():
                            "parallelism": f"replicas x{ws}",
                            "tile": f"{tinfo.tile_cells} cells per block, "
                                    f"{'one thread per cell' if tinfo.threads_per_cell == 1 else 'one thread per cell and species'}, "
-                                   f"{tinfo.tile_min_blocks} blocks/SM, {tinfo.neighbour_bits}-bit "
-                                   f"neighbour table (autotuned)",
+                                   f"{tinfo.tile_min_blocks} blocks/SM, " + (
+                                       "neighbours decoded from per-row fluid bitmasks" if tinfo.neighbour_bits == 1
+                                       else f"{tinfo.neighbour_bits}-bit neighbour table") + " (autotuned)",
                            "l2": "state larger than L2 (no flush needed)" if nf * bpc > 129e6 * 2
                            else "state fits in L2"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps, "time_to_residual": ttr}
+                "gpu_launches": args.steps, "fp16_storage": fp16, "time_to_residual": ttr}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
     return 0
 
 
-def sweep_cases(args):
+def sweep_cases(args, scale=None):
     """The uneven-size sweep: each microstructure at each operating point."""
     from workloads import cases as W
-    structs = W.sweep_structures(args.sweep_2d, args.sweep_3d, scale=args.sweep_scale)
+    structs = W.sweep_structures(args.sweep_2d, args.sweep_3d,
+                                 scale=args.sweep_scale if scale is None else scale)
     pts = W.sweep_operating_points(args.sweep_points)
     groups = {2: [], 3: []}
     for st in structs:
@@ -551,32 +716,21 @@ def main_table2(args, ws, rank, local):
     return 0
 
 
-def main_sweep(args, ws, rank, local):
-    """Many microstructures x operating points: one launch per lattice and
-    step (batched, autotuned tile) against stepping every case in a handle
-    of its own."""
+def _batched_steps(L, groups, precision, steps, warmup, stream, dist):
+    """Every case of each lattice group in one batch (one launch per lattice
+    and step); CUDA-event time of `steps` steps over all batches."""
     import torch
-    torch.cuda.set_device(local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    from paper_1809_01600_gb300 import lbms as L
-    L.load()
-    groups = sweep_cases(args)
     batches = []
     for dim in (2, 3):
         cs = groups[dim]
         if not cs:
             continue
-        b = L.Batch.from_cases(cs, precision=args.precision)
+        b = L.Batch.from_cases(cs, precision=precision)
         for k, c in enumerate(cs):
             b.set_bc(c.x_in, c.current_A_cm2, case=k)
         batches.append((dim, cs, b))
-    nf = sum(c.n_fluid for _, cs, _ in batches for c in cs)
-    stream = torch.cuda.current_stream()
     for _, _, b in batches:
-        b.step(args.warmup)
+        b.step(warmup)
         b.step(32)
     torch.cuda.synchronize()
     clocks = ClockSampler(torch.cuda.current_device())
@@ -588,43 +742,87 @@ def main_sweep(args, ws, rank, local):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _, _, b in batches:
-        b.step(args.steps)
+        b.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    t_dev = ms / 1e3
-    t_dev = max_over_ranks(dist, t_dev, "cuda")
-    units = nf * 3 * args.steps * ws
-    value = units / t_dev / 1e6
-    tiles = {dim: "%d cells, %d blocks/SM" % (b.info().tile_cells, b.info().tile_min_blocks)
-             for dim, _, b in batches}
-    etas = {dim: b.overpotentials(raise_on_fail=False)[0] for dim, _, b in batches}
+    tiles = {dim: "%d cells, %d blocks/SM, nb%d" % (b.info().tile_cells, b.info().tile_min_blocks,
+                                                     b.info().neighbour_bits) for dim, _, b in batches}
+    etas = [b.overpotentials(raise_on_fail=False)[0] for _, _, b in batches]
     for _, _, b in batches:
         b.close()
+    return ms, clk, tiles, etas, len(batches)
 
-    # the same cases, one handle each, stepped one after another
-    seq_steps = max(1, min(args.steps, 200))
-    t_seq = 0.0
+
+def _sequential_steps(L, groups, precision, steps, stream):
+    """The same cases, one handle each, stepped one after another: summed
+    CUDA-event time of `steps` steps per handle."""
+    import torch
+    t = 0.0
     for dim in (2, 3):
         for c in groups[dim]:
-            s = L.Solver.from_case(c, precision=args.precision)
+            s = L.Solver.from_case(c, precision=precision)
             s.set_bc(c.x_in, c.current_A_cm2)
             s.step(32)
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True)
             a1 = torch.cuda.Event(enable_timing=True)
             a0.record(stream)
-            s.step(seq_steps)
+            s.step(steps)
             a1.record(stream)
             torch.cuda.synchronize()
-            t_seq += a0.elapsed_time(a1) / 1e3
+            t += a0.elapsed_time(a1) / 1e3
             s.close()
-    seq_value = nf * 3 * seq_steps / t_seq / 1e6
+    return t
+
+
+def main_sweep(args, ws, rank, local):
+    """The batched sweep: --sweep-2d 2-D and --sweep-3d 3-D seeded
+    microstructures of uneven size, each at --sweep-points operating points,
+    one launch per lattice and step (batched, autotuned tile).  Then the
+    same recipe with grids scaled by --sweep-small-scale, where the cases are
+    small enough that one launch per case leaves the GPU idle: batched
+    against one handle per case."""
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1809_01600_gb300 import lbms as L
+    L.load()
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    groups = sweep_cases(args)
+    t_gen = time.perf_counter() - t_gen
+    nf = sum(c.n_fluid for d in (2, 3) for c in groups[d])
+    ms, clk, tiles, etas, nlaunch = _batched_steps(L, groups, args.precision, args.steps, args.warmup, stream, dist)
+    t_dev = max_over_ranks(dist, ms / 1e3, "cuda")
+    units = nf * 3 * args.steps * ws
+    value = units / t_dev / 1e6
     bpc = {d: bytes_per_cell(d, args.precision) for d in (2, 3)}
-    alg = sum(c.n_fluid * bpc[c.dim] for _, cs, _ in batches for c in cs)
+    alg = sum(c.n_fluid * bpc[c.dim] for d in (2, 3) for c in groups[d])
     achieved = alg / (t_dev / args.steps) / 1e9
     peak, peak_kind = measured_peak_hbm()
+    eta_all = np.concatenate([np.asarray(e) for e in etas])
+
+    small = None
+    if args.sweep_small_scale > 0:
+        sg = sweep_cases(args, scale=args.sweep_small_scale)
+        snf = sum(c.n_fluid for d in (2, 3) for c in sg[d])
+        sms, sclk, stiles, _, _ = _batched_steps(L, sg, args.precision, args.steps, args.warmup, stream, None)
+        seq_steps = max(1, min(args.steps, 200))
+        t_seq = _sequential_steps(L, sg, args.precision, seq_steps, stream)
+        bval = snf * 3 * args.steps / (sms / 1e3) / 1e6
+        sval = snf * 3 * seq_steps / t_seq / 1e6
+        small = {"cases": {"2d": len(sg[2]), "3d": len(sg[3])}, "fluid_cells": snf,
+                 "scale": args.sweep_small_scale, "batched": {"value": round(bval, 2), "unit": METRIC,
+                                                              "ms_per_step": round(sms / args.steps, 5),
+                                                              "tiles": stiles, "clocks": sclk},
+                 "sequential": {"value": round(sval, 2), "unit": METRIC, "steps": seq_steps,
+                                "what": "the same cases, one handle each, stepped one after another"},
+                 "speedup_vs_sequential": round(bval / sval, 2)}
     if rank == 0:
         n2, n3 = len(groups[2]), len(groups[3])
         line = {"metric": METRIC, "value": round(value, 2), "unit": METRIC, "n_gpus": ws,
@@ -636,16 +834,12 @@ def main_sweep(args, ws, rank, local):
                                        f"x {args.sweep_points} operating points",
                            "cases": {"2d": n2, "3d": n3}, "fluid_cells": nf, "precision": args.precision,
                            "tiles": tiles, "parallelism": f"replicas x{ws}",
-                           "launches_per_step": len(batches)},
+                           "launches_per_step": nlaunch, "host_generation_seconds": round(t_gen, 1)},
                 "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                              "frac": round(achieved / peak, 4), "traffic": None, "peak_source": peak_kind},
-                "sequential": {"value": round(seq_value, 2), "unit": METRIC,
-                               "what": "the same cases, one handle each, stepped one after another",
-                               "steps": seq_steps},
-                "speedup_vs_sequential": round(value / seq_value, 2),
-                "eta_V_range": [float(np.nanmin(np.concatenate(list(etas.values())))),
-                                float(np.nanmax(np.concatenate(list(etas.values()))))],
-                "clocks": clk, "gpu_launches": args.steps * len(batches)}
+                "small_cases": small,
+                "eta_V_range": [float(np.nanmin(eta_all)), float(np.nanmax(eta_all))],
+                "clocks": clk, "gpu_launches": args.steps * nlaunch}
         print(json.dumps(line))
     if dist:
         dist.destroy_process_group()
@@ -653,25 +847,44 @@ def main_sweep(args, ws, rank, local):
 
 
 def main_reference(args, ws, rank):
+    """The oracle arm: the FP64 CPU oracle timed on every host core, one
+    process per z-slab of the same workload, bounded to about 150 s; with
+    --oracle-ttr, the oracle's own time to residual on the workload (one
+    process: a single small case)."""
     if rank != 0:
         return 0
     case = make_case(args.workload)
-    budget = 150.0
-    sample, planes = oracle_sample(case, budget, args.steps + args.warmup)
-    t = run_oracle(sample, args.steps, args.warmup)
-    value = sample.n_fluid * 3 * args.steps / t / 1e6
-    desc = (f"FP64 CPU oracle on the first {planes} z-planes of the {case.name} mask "
-            f"({sample.n_fluid} fluid cells, periodic in z), {args.steps} timed steps")
+    nz = case.solid.shape[0]
+    procs = max(1, min(args.oracle_procs or os.cpu_count() or 1, nz))
+    probe = case.with_(solid=np.ascontiguousarray(case.solid[:1]))
+    t_plane = run_oracle(probe, 1, 1)                  # seconds per z-plane and step
+    per_proc = max(1, int(150.0 / max(t_plane * (args.steps + args.warmup), 1e-9)))
+    planes = min(nz, procs * per_proc)
+    cells, wall, procs, planes = oracle_all_cores(args.workload, args.steps, args.warmup, procs, planes)
+    value = cells * 3 * args.steps / wall / 1e6
+    desc = (f"FP64 CPU oracle, {args.steps} timed steps (after {args.warmup}) on the first {planes} of "
+            f"{nz} z-planes of the {case.name} mask ({cells} fluid cells), split into {procs} z-slabs "
+            f"(each periodic in z) run concurrently by {procs} single-threaded processes")
     line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": METRIC,
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(t / args.steps * 1e3, 3), "higher_is_better": True,
+            "ms_per_step": round(wall / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": case.name, "precision": args.precision,
-                       "parallelism": "host cores"},
-            "cpu_baseline": {"value": round(value, 4), "unit": METRIC, "cores": cores_used(),
+                       "parallelism": f"{procs} host cores"},
+            "cpu_baseline": {"value": round(value, 4), "unit": METRIC, "cores": procs * cores_used(),
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": round(value, 4), "unit": METRIC, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if args.oracle_ttr:
+        from oracle import Oracle
+        o = Oracle(case)
+        t = time.perf_counter()
+        n, r = o.run_to_residual(args.time_to_residual or 1e-8, args.max_steps, 100)
+        secs = time.perf_counter() - t
+        line["time_to_residual"] = {"tol": args.time_to_residual or 1e-8, "steps": int(n), "residual": r,
+                                    "seconds": round(secs, 2), "eta_V": o.overpotential(), "cores": 1,
+                                    "what": "the FP64 oracle run to the residual on the whole workload "
+                                            "from the uniform inlet start (one process)"}
     print(json.dumps(line))
     return 0
 

@@ -65,3 +65,24 @@ def test_reference_arm_runs_on_rank_0_only(capsys):
     args = type("A", (), dict(workload="anode3d_256x128x128", steps=2, warmup=3, precision="fp32"))()
     assert bench.main_reference(args, 2, 1) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_on_all_cores_covers_the_workload(capsys):
+    """The CPU baseline splits the workload's z-planes over processes (spawned,
+    each a single-threaded oracle on its slab, periodic in z); together they
+    cover every fluid cell, and the reference arm reports the core count."""
+    sys.path.insert(0, ROOT)
+    import json
+    import bench
+    from workloads import cases
+    case = cases.anode_3d_small()
+    cells, wall, procs, planes = bench.oracle_all_cores("anode3d_small", 2, 1, procs=2)
+    assert procs == 2 and planes == case.solid.shape[0]
+    assert cells == case.n_fluid and wall > 0
+    args = type("A", (), dict(workload="anode3d_small", steps=2, warmup=1, precision="fp64",
+                              oracle_procs=2, oracle_ttr=False, time_to_residual=1e-8,
+                              max_steps=10))()
+    assert bench.main_reference(args, 1, 0) == 0
+    line = json.loads(capsys.readouterr().out.strip())
+    assert line["impl"] == "reference" and line["cpu_baseline"]["cores"] == 2
+    assert line["value"] > 0 and line["e2e"]["h2d_bytes_per_step"] == 0

@@ -138,7 +138,9 @@ def sweep_structures(n2d: int, n3d: int, seed0: int = 100, scale: float = 1.0):
     times ``scale``), radius 2-6 cells, porosity uniform in [0.30, 0.55] in
     3-D and in [0.42, 0.55] in 2-D, where the pore space of overlapping disks
     stops percolating near 0.32 and long strips rarely percolate below 0.4.
-    Returns a list of Cases with default boundary data."""
+    A structure none of whose draws percolates is drawn again with its
+    porosity raised by 0.02 until one does (the case records the porosity
+    reached).  Returns a list of Cases with default boundary data."""
     rng = np.random.Generator(np.random.PCG64(seed0))
     out = []
     for k in range(n2d + n3d):
@@ -154,8 +156,16 @@ def sweep_structures(n2d: int, n3d: int, seed0: int = 100, scale: float = 1.0):
         else:
             n = int(round(rng.uniform(64, 160) * scale / 8)) * 8
             shape = (max(n, 16),) * 3
-        out.append(porous(shape, radius=rad, porosity=por, seed=seed,
-                          name=f"sweep{k}_{'x'.join(map(str, shape[::-1]))}_eps{por:.2f}_r{rad}"))
+        while True:
+            try:
+                c = porous(shape, radius=rad, porosity=por, seed=seed,
+                           name=f"sweep{k}_{'x'.join(map(str, shape[::-1]))}_eps{por:.2f}_r{rad}")
+                break
+            except RuntimeError:
+                if por > 0.7:
+                    raise
+                por = round(por + 0.02, 4)
+        out.append(c)
     return out
 
 
