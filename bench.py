@@ -95,6 +95,15 @@ def parse():
     ap.add_argument("--ws-test", type=int, default=16, help="warm start: held-out anodes")
     ap.add_argument("--ws-iters", type=int, default=6000, help="warm start: Adam steps")
     ap.add_argument("--ws-lr", type=float, default=1e-3, help="warm start: peak learning rate")
+    ap.add_argument("--ws-test-shape", default="64x32x32",
+                    help="warm start: grid (nx x ny x nz) of the held-out anodes")
+    ap.add_argument("--ws-train-test-shape", type=int, default=0,
+                    help="warm start: training anodes at the held-out grid, added to the 64x32x32 ones")
+    ap.add_argument("--ws-plain", action="store_true",
+                    help="warm start: also time plain FP32 (no extrapolation) from each start")
+    ap.add_argument("--ws-compare-unet", action="store_true",
+                    help="warm start: also train a 3-D U-Net (PyTorch convolutions, a measured comparison "
+                         "for the choice of the pointwise network) on the same data and time its starts")
     return ap.parse_args()
 
 
@@ -590,19 +599,40 @@ def sweep_cases(args, scale=None):
     return groups
 
 
-def train_warmstart_net(L, train, tol, args):
-    """Steady states of the training anodes (one batch, FP32 + extrapolation)
-    and a warm-start network trained on them; returns the net and timings."""
+def extrapolate_every_for(nx):
+    """W of the single-mode extrapolation for an anode nx cells long: the
+    slowest mode decays as 1/nx^2, so W scales with nx^2 (20,000 steps at
+    nx = 256), rounded to 500 steps, at least 1000."""
+    return max(1000, int(round(20000 * (nx / 256.0) ** 2 / 500.0)) * 500)
+
+
+def rre_every(nx):
+    """Snapshot spacing W of the reduced-rank extrapolation for an anode nx
+    cells long: the slowest mode decays as 1/nx^2, so W scales with nx^2
+    (10,000 steps at nx = 256), rounded to 500 steps, at least 1000."""
+    return max(1000, int(round(10000 * (nx / 256.0) ** 2 / 500.0)) * 500)
+
+
+def train_warmstart_net(L, train, tol, args, keep=None):
+    """Steady states of the training anodes (one batch, FP32 + slowest-mode
+    extrapolation) and a warm-start network trained on them; returns the net
+    and timings.  With a list `keep`, each training case's dense input volume
+    and target (for the convolutional comparison) are appended to it."""
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    b = L.Batch.from_cases(train, precision="fp32", extrapolate_every=5000)
+    nx_max = max(c.solid.shape[2] for c in train)
+    b = L.Batch.from_cases(train, precision="fp32", extrapolate_every=extrapolate_every_for(nx_max))
     for k, c in enumerate(train):
         b.set_bc(c.x_in, c.current_A_cm2, case=k)
     n, _, _, st = b.run_to_residual(tol, args.max_steps, raise_on_fail=False)
     net = L.Net(width=704, depth=3, seed=1)
     for k in range(len(train)):
         net.add_sample(b, k)
+        if keep is not None:
+            V = _dense_inputs(net, b, train[k], k)
+            X = b.fields(k).astype(np.float32)
+            keep.append((V, 100.0 * (X - V[0:3]) * V[16:17]))
     b.close()
     t1 = time.perf_counter()
     loss = net.train(args.ws_iters, batch=8192, lr=args.ws_lr)
@@ -614,33 +644,148 @@ def train_warmstart_net(L, train, tol, args):
                               "final_loss": loss, "seconds": round(t2 - t1, 2)}}
 
 
+# ------------------------------------------------- warm-start comparison
+def _dense_inputs(net, handle, case, k):
+    """Dense input volume [C, nz, ny, nx] of one case for the convolutional
+    comparison: the 16 used feature columns of lbms_net_features scattered
+    to the fluid voxels, plus the fluid mask."""
+    F = net.features(handle, case.n_fluid, case=k)[:, :16]
+    nz, ny, nx = case.solid.shape
+    fl = np.flatnonzero(~case.solid.reshape(-1))
+    V = np.zeros((17, nz * ny * nx), dtype=np.float32)
+    V[:16, fl] = F.T
+    V[16, fl] = 1.0
+    return V.reshape(17, nz, ny, nx)
+
+
+def _unet(torch, width=28):
+    """A three-level 3-D U-Net (two 3x3x3 convolutions per level, ReLU,
+    max-pool down, transposed convolution up, skip concatenation), about
+    1M parameters at width 28."""
+    nn = torch.nn
+
+    def block(ci, co):
+        return nn.Sequential(nn.Conv3d(ci, co, 3, padding=1), nn.ReLU(), nn.Conv3d(co, co, 3, padding=1), nn.ReLU())
+
+    class UNet(nn.Module):
+        def __init__(self):
+            super().__init__()
+            w = width
+            self.e1, self.e2, self.e3 = block(17, w), block(w, 2 * w), block(2 * w, 4 * w)
+            self.u2 = nn.ConvTranspose3d(4 * w, 2 * w, 2, stride=2)
+            self.d2 = block(4 * w, 2 * w)
+            self.u1 = nn.ConvTranspose3d(2 * w, w, 2, stride=2)
+            self.d1 = block(2 * w, w)
+            self.out = nn.Conv3d(w, 3, 1)
+
+        def forward(self, x):
+            a = self.e1(x)
+            b = self.e2(nn.functional.max_pool3d(a, 2))
+            c = self.e3(nn.functional.max_pool3d(b, 2))
+            d = self.d2(torch.cat([self.u2(c), b], 1))
+            e = self.d1(torch.cat([self.u1(d), a], 1))
+            return self.out(e)
+
+    return UNet()
+
+
+def compare_unet(L, net, kept, test, tol, prec, Wx, modes, args):
+    """The convolutional alternative to the pointwise network: a 3-D U-Net
+    trained with PyTorch on the same steady states (`kept`: input volumes
+    and targets 100 (X - X_profile) on fluid voxels; mean-square error,
+    Adam), then used as the start of the same held-out runs.  Returns its
+    mean steps and timings."""
+    import torch
+    dev = torch.device("cuda")
+    data = {}
+    for V, T in kept:
+        data.setdefault(V.shape, []).append((V, T))
+    model = _unet(torch).to(dev)
+    nparams = sum(p.numel() for p in model.parameters())
+    opt = torch.optim.Adam(model.parameters(), lr=1e-3)
+    iters = args.ws_iters
+    sched = torch.optim.lr_scheduler.CosineAnnealingLR(opt, iters, eta_min=5e-5)
+    groups = {sh: (torch.tensor(np.stack([v for v, _ in d]), device=dev),
+                   torch.tensor(np.stack([t for _, t in d]), device=dev)) for sh, d in data.items()}
+    keys = list(groups)
+    gen = torch.Generator(device="cpu").manual_seed(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(iters):
+        Vg, Tg = groups[keys[it % len(keys)]]
+        idx = torch.randint(0, Vg.shape[0], (min(8, Vg.shape[0]),), generator=gen).to(dev)
+        pred = model(Vg[idx])
+        m = Vg[idx, 16:17]
+        loss = (((pred - Tg[idx]) * m) ** 2).sum() / (3.0 * m.sum())
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        sched.step()
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx, extrapolate_modes=modes)
+    for k, c in enumerate(test):
+        bt.set_bc(c.x_in, c.current_A_cm2, case=k)
+    torch.cuda.synchronize()
+    ta = time.perf_counter()
+    with torch.no_grad():
+        for k, c in enumerate(test):
+            V = _dense_inputs(net, bt, c, k)
+            P = model(torch.tensor(V[None], device=dev))[0].cpu().numpy()
+            X = np.maximum(V[0:3] + P / 100.0, 1e-6)
+            X = X / X.sum(axis=0, keepdims=True)
+            bt.set_fields(k, np.where(c.solid[None], 0.0, X))
+    torch.cuda.synchronize()
+    tb_ = time.perf_counter()
+    n, steps, r, st = bt.run_to_residual(tol, args.max_steps, raise_on_fail=False)
+    torch.cuda.synchronize()
+    tc = time.perf_counter()
+    bt.close()
+    return {"params": int(nparams), "iters": iters, "final_loss": float(loss.detach()),
+            "train_seconds": round(t_train, 2), "mean_steps": float(np.mean(steps)), "max_steps": int(np.max(steps)),
+            "converged": bool(np.all(steps > 0)), "start_seconds": round(tb_ - ta, 3),
+            "batch_seconds": round(tc - tb_, 2),
+            "model": "3-D U-Net, 3 levels, widths 28/56/112, PyTorch convolutions (comparison only)"}
+
+
 def main_warmstart(args, ws, rank, local):
-    """Learned warm start: steady states of seeded 64x32x32 anodes from the
-    batched solver train the network; on held-out anodes, the steps to
-    residual 1e-8 from the uniform start, the 1-D profile of Section 4.1 and
-    the network's prediction (plain FP32, and FP16 storage + extrapolation)."""
+    """Learned warm start: steady states of seeded 64x32x32 anodes (and, with
+    --ws-train-test-shape, of anodes at the held-out grid) from the batched
+    solver train the network; on held-out anodes of --ws-test-shape, the
+    steps and time to residual 1e-8 from the uniform start, the 1-D profile
+    of Section 4.1 and the network's prediction, for the chosen form (FP16
+    storage + slowest-mode extrapolation) and, with --ws-plain, plain FP32."""
     import torch
     torch.cuda.set_device(local)
     from paper_1809_01600_gb300 import lbms as L
     from workloads import cases as W
     L.load()
     tol = args.time_to_residual or 1e-8
+    nx, ny, nz = (int(v) for v in args.ws_test_shape.split("x"))
+    tshape = (nz, ny, nx)
     train = W.warmstart_cases(args.ws_train, 1000)
-    test = W.warmstart_cases(args.ws_test, 5000)
-    out = {"residual": tol}
-
-    net, info = train_warmstart_net(L, train, tol, args)
+    if args.ws_train_test_shape:
+        train += W.warmstart_cases(args.ws_train_test_shape, 3000, shape=tshape)
+    test = W.warmstart_cases(args.ws_test, 5000, shape=tshape)
+    out = {"residual": tol, "test_shape": args.ws_test_shape, "train": {"64x32x32": args.ws_train,
+                                                                       args.ws_test_shape: args.ws_train_test_shape}}
+    kept = [] if args.ws_compare_unet else None
+    net, info = train_warmstart_net(L, train, tol, args, keep=kept)
     out.update(info)
-
-    forms = (("plain_fp32", "fp32", 0), ("fp16_extrapolated", "fp16", 5000))
-    for label, prec, Wx in forms:
-        res = {}
+    Wx = extrapolate_every_for(nx)
+    forms = [("fp16_extrapolated", "fp16", Wx, 1)]
+    if args.ws_plain:
+        forms.insert(0, ("plain_fp32", "fp32", 0, 1))
+    for label, prec, Wx, modes in forms:
+        res = {"extrapolate_every": Wx, "extrapolate_modes": modes}
         for start in ("uniform", "profile1d", "network"):
-            bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx,
+            bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx, extrapolate_modes=modes,
                                     init_mode="profile1d" if start == "profile1d" else "uniform")
             for k, c in enumerate(test):
                 bt.set_bc(c.x_in, c.current_A_cm2, case=k)
             torch.cuda.synchronize()
+            clocks = ClockSampler(torch.cuda.current_device())
+            clocks.start()
             ta = time.perf_counter()
             if start == "network":
                 for k in range(len(test)):
@@ -652,19 +797,26 @@ def main_warmstart(args, ws, rank, local):
             tc = time.perf_counter()
             res[start] = {"mean_steps": float(np.mean(steps)), "max_steps": int(np.max(steps)),
                           "converged": bool(np.all(steps > 0)), "start_seconds": round(tb - ta, 3),
-                          "batch_seconds": round(tc - tb, 2)}
+                          "batch_seconds": round(tc - tb, 2), "clocks": clocks.stop()}
             bt.close()
-        for start in ("profile1d", "network"):
-            res[start]["steps_vs_uniform"] = round(res[start]["mean_steps"] / res["uniform"]["mean_steps"], 3)
+        if args.ws_compare_unet and label == "fp16_extrapolated":
+            res["unet"] = compare_unet(L, net, kept, test, tol, prec, Wx, modes, args)
+        for start in ("profile1d", "network", "unet"):
+            if start in res:
+                res[start]["steps_vs_uniform"] = round(res[start]["mean_steps"] / res["uniform"]["mean_steps"], 3)
         out[label] = res
+    tc, ms = net.gemm_calls()
+    out["gemm_calls"] = {"tcgen05": tc, "mma_sync": ms}
     net.close()
     if rank == 0:
-        v = out["plain_fp32"]["network"]["mean_steps"]
-        line = {"metric": "steps to residual (held-out anodes, network start)", "value": v, "unit": "steps",
-                "n_gpus": 1, "higher_is_better": False, "vs_baseline": None, "dtype": "bf16 network, f32 LBM",
-                "data": "synthetic",
-                "config": {"workload": f"learned warm start, {len(train)} training + {len(test)} held-out "
-                                       f"64x32x32 D3Q19 anodes"},
+        v = out["fp16_extrapolated"]["network"]["mean_steps"]
+        line = {"metric": "steps to residual (held-out anodes, network start, FP16 + extrapolation)", "value": v,
+                "unit": "steps", "n_gpus": 1, "higher_is_better": False, "vs_baseline": None,
+                "dtype": "bf16 network, f32 LBM", "data": "synthetic",
+                "config": {"workload": f"learned warm start, {len(train)} training anodes "
+                                       f"({args.ws_train} 64x32x32 + {args.ws_train_test_shape} "
+                                       f"{args.ws_test_shape}) and {len(test)} held-out {args.ws_test_shape} "
+                                       f"D3Q19 anodes"},
                 "warm_start": out}
         print(json.dumps(line))
     return 0
@@ -716,19 +868,29 @@ def main_table2(args, ws, rank, local):
     return 0
 
 
+BATCH_MAX_CELLS = 100_000_000   # a batch's link offsets (link x row stride) stay 32-bit for D3Q19
+
+
 def _batched_steps(L, groups, precision, steps, warmup, stream, dist):
-    """Every case of each lattice group in one batch (one launch per lattice
-    and step); CUDA-event time of `steps` steps over all batches."""
+    """The cases of each lattice group in as few batches as the step
+    kernel's 32-bit in-species offsets allow (at most BATCH_MAX_CELLS fluid
+    cells each; one launch per batch and step); CUDA-event time of `steps`
+    steps over all batches."""
     import torch
     batches = []
     for dim in (2, 3):
-        cs = groups[dim]
-        if not cs:
-            continue
-        b = L.Batch.from_cases(cs, precision=precision)
-        for k, c in enumerate(cs):
-            b.set_bc(c.x_in, c.current_A_cm2, case=k)
-        batches.append((dim, cs, b))
+        chunk, cells = [], 0
+        for c in groups[dim] + [None]:
+            if c is not None and (not chunk or cells + c.n_fluid <= BATCH_MAX_CELLS):
+                chunk.append(c)
+                cells += c.n_fluid
+                continue
+            if chunk:
+                b = L.Batch.from_cases(chunk, precision=precision)
+                for k, cc in enumerate(chunk):
+                    b.set_bc(cc.x_in, cc.current_A_cm2, case=k)
+                batches.append((dim, chunk, b))
+            chunk, cells = ([c], c.n_fluid) if c is not None else ([], 0)
     for _, _, b in batches:
         b.step(warmup)
         b.step(32)
@@ -747,8 +909,8 @@ def _batched_steps(L, groups, precision, steps, warmup, stream, dist):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    tiles = {dim: "%d cells, %d blocks/SM, nb%d" % (b.info().tile_cells, b.info().tile_min_blocks,
-                                                     b.info().neighbour_bits) for dim, _, b in batches}
+    tiles = ["%dD x%d: %d cells, %d blocks/SM, nb%d" % (dim, len(cs), b.info().tile_cells, b.info().tile_min_blocks,
+                                                         b.info().neighbour_bits) for dim, cs, b in batches]
     etas = [b.overpotentials(raise_on_fail=False)[0] for _, _, b in batches]
     for _, _, b in batches:
         b.close()

@@ -108,7 +108,8 @@ typedef struct {
  *  extrapolate_modes  how the extrapolation every W steps works: 0 or 1:
  *             the single-mode jump above; M in 2..6: reduced-rank
  *             extrapolation (RRE) over M + 1 snapshots of X taken W steps
- *             apart, X = sum_j gamma_j x_j with gamma minimising
+ *             apart (the first W / 8 steps after the start or the last jump,
+ *             past the fast transient), X = sum_j gamma_j x_j with gamma minimising
  *             || sum_j gamma_j (x_{j+1} - x_j) || subject to sum_j gamma_j = 1
  *             (per case, FP64), which removes up to M - 1 decay modes at once;
  *             a case whose snapshot differences do not shrink is left alone.

@@ -663,9 +663,11 @@ lbms_status rre_begin(lbms_ctx* c, Extrapolator& ex) {
     ex.rre_coef.assign((size_t)L.n_cases * m, 0.0);
     ex.coef.assign(L.n_cases, 0.0);
     ex.polish.assign(L.n_cases, 0);
-    ex.since = 0;
-    CK(launch_rre_snapshot(L, 0, c->stream), "extrapolation snapshot");
-    ex.rre_n = 1;
+    // the first snapshot of a cycle waits W / 8 steps, past the fast
+    // transient that follows a start or a jump (it does not decay
+    // geometrically and would corrupt the first difference)
+    ex.rre_n = 0;
+    ex.since = c->opt.extrapolate_every - std::max<int64_t>(1, c->opt.extrapolate_every / 8);
     return LBMS_OK;
 }
 
@@ -679,7 +681,7 @@ lbms_status rre_check(lbms_ctx* c, Extrapolator& ex) {
     ex.since = 0;
     for (int k = 0; k < n; ++k) ex.coef[k] = 0.0;
     CK(launch_rre_snapshot(L, ex.rre_n, c->stream), "extrapolation snapshot");
-    ++ex.rre_n;
+    if (ex.rre_n++ == 0) return LBMS_OK;
     // a full cycle, or an early one (at least two differences) for the
     // final extrapolation of cases that met tol; an early cycle moves only
     // those cases
@@ -706,7 +708,8 @@ lbms_status rre_check(lbms_ctx* c, Extrapolator& ex) {
        "extrapolation coefficients");
     c->h2d += ex.rre_coef.size() * sizeof(double);
     CK(launch_rre_apply(L, mm, c->stream), "extrapolation kernel");
-    ex.rre_n = 1;
+    ex.rre_n = 0;
+    ex.since = c->opt.extrapolate_every - std::max<int64_t>(1, c->opt.extrapolate_every / 8);
     return LBMS_OK;
 }
 
@@ -864,7 +867,9 @@ lbms_status lbms_create_batch(int n_cases, const lbms_geometry* geoms, const lbm
         cs.nf = (int)cs.fluid_cell.size();
         cs.base = (int)next;
         next += ((int64_t)cs.nf + kCaseAlign - 1) / kCaseAlign * kCaseAlign;
-        if (next >= (int64_t)std::numeric_limits<int>::max() / 32)
+        // cell indices are 32-bit; the per-species offsets (link x row stride)
+        // are bounded by the Q x stride check below
+        if (next >= (int64_t)std::numeric_limits<int>::max() - kCaseAlign)
             return bail(fail(c, LBMS_EINVAL, "too many fluid cells for 32-bit indices"));
         cs.row_first = (int)rows_x0.size();
         cs.nrows = cs.ny * cs.nz;

@@ -1063,8 +1063,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_gram_kernel(const double* __r
 }
 
 // X += sum_a c_a u_a with the case's coefficients coef[case * M + a], in both
-// X copies (the step's and the lagged one); slot 0 takes the new X, the first
-// snapshot of the next cycle.
+// X copies (the step's and the lagged one); slot 0 also takes the new X.
 template <typename XS, int M>
 __global__ void __launch_bounds__(kSegThreads) seg_rre_apply_kernel(XS* __restrict__ X, XS* __restrict__ Xprev,
                                                                     double* __restrict__ ring, int64_t S,
