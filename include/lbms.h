@@ -97,11 +97,13 @@ typedef struct {
  *             W-step changes of X, X += rho / (1 - rho) * (last change) when
  *             two successive ratios agree within 2 % and 0.05 < rho < 0.98).
  *             The fixed point is unchanged; only the approach is shortened.
- *             With W > 0, a case that meets tol is not done yet: one final
+ *             With W > 0, a case that meets tol is not done yet: a final
  *             extrapolation is taken at its next W-step check (from the
  *             last two W-step changes, or from the snapshots of the current
- *             reduced-rank cycle, see extrapolate_modes), and the case is
- *             done when it meets tol again after it.  The residual measures
+ *             reduced-rank cycle, see extrapolate_modes), repeated (at most
+ *             three times) while the single-mode jump moved X by more than
+ *             1e-5 of |X|, and the case is done when it meets tol again
+ *             after the last one.  The residual measures
  *             the rate of change, so the error it leaves is largest along
  *             the slowest mode; the final extrapolation removes most of it.
  *             0 = off [0]

@@ -521,7 +521,14 @@ struct Extrapolator {
     int rre_n = 0;                     // snapshots taken in the current reduced-rank cycle
     std::vector<double> rre_coef;      // [cases][order]
     std::vector<int> polish;           // per case: 0 not yet at tol, 1 final extrapolation pending, 2 done
+    std::vector<int> polish_n;         // final extrapolations taken per case
 };
+
+// The final extrapolation of a case repeats while its jump moved X by more
+// than kPolishRel of |X| (it removes most, not all, of the slowest mode), at
+// most kPolishMax times.
+constexpr double kPolishRel = 1e-5;
+constexpr int kPolishMax = 3;
 
 lbms_status extrap_begin(lbms_ctx* c, Extrapolator& ex) {
     const int n = c->L.n_cases;
@@ -534,6 +541,7 @@ lbms_status extrap_begin(lbms_ctx* c, Extrapolator& ex) {
     ex.rho_prev.assign(n, -1.0);
     ex.coef.assign(n, 0.0);
     ex.polish.assign(n, 0);
+    ex.polish_n.assign(n, 0);
     ex.since = 0;
     // E = X (coefficient 0 leaves X alone)
     CK(cudaMemcpyAsync(c->L.b.coef, ex.coef.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream), "coef");
@@ -555,7 +563,9 @@ lbms_status extrap_check(lbms_ctx* c, Extrapolator& ex) {
             // mode dominates both W-step changes, so one ratio suffices
             const double rho = nrm / ex.norm_prev[k];
             if (rho > 0.05 && rho < 0.98) cf = rho / (1.0 - rho);
-            ex.polish[k] = 2;
+            const double xn = std::sqrt(o[3] + o[4] + o[5]);
+            const bool again = cf > 0.0 && xn > 0.0 && cf * nrm > kPolishRel * xn && ++ex.polish_n[k] < kPolishMax;
+            ex.polish[k] = again ? 1 : 2;
             ex.norm_prev[k] = -1.0;
             ex.rho_prev[k] = -1.0;
         } else if (ex.norm_prev[k] > 0.0 && std::isfinite(nrm)) {
@@ -663,6 +673,7 @@ lbms_status rre_begin(lbms_ctx* c, Extrapolator& ex) {
     ex.rre_coef.assign((size_t)L.n_cases * m, 0.0);
     ex.coef.assign(L.n_cases, 0.0);
     ex.polish.assign(L.n_cases, 0);
+    ex.polish_n.assign(L.n_cases, 0);
     // the first snapshot of a cycle waits W / 8 steps, past the fast
     // transient that follows a start or a jump (it does not decay
     // geometrically and would corrupt the first difference)
