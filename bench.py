@@ -102,8 +102,11 @@ def parse():
     ap.add_argument("--ws-plain", action="store_true",
                     help="warm start: also time plain FP32 (no extrapolation) from each start")
     ap.add_argument("--ws-compare-unet", action="store_true",
-                    help="warm start: also train a 3-D U-Net (PyTorch convolutions, a measured comparison "
-                         "for the choice of the pointwise network) on the same data and time its starts")
+                    help="warm start: also train the same 3-D U-Net with PyTorch convolutions (a comparison "
+                         "arm for the U-Net on this project's kernels) on the same data and time its starts")
+    ap.add_argument("--ws-unet-iters", type=int, default=6000,
+                    help="warm start: Adam steps of the 3-D U-Net on this project's kernels (0 skips it)")
+    ap.add_argument("--ws-unet-width", type=int, default=28, help="warm start: U-Net width (28: 1.05M parameters)")
     return ap.parse_args()
 
 
@@ -613,11 +616,12 @@ def rre_every(nx):
     return max(1000, int(round(10000 * (nx / 256.0) ** 2 / 500.0)) * 500)
 
 
-def train_warmstart_net(L, train, tol, args, keep=None):
+def train_warmstart_net(L, train, tol, args, keep=None, unet=None):
     """Steady states of the training anodes (one batch, FP32 + slowest-mode
     extrapolation) and a warm-start network trained on them; returns the net
     and timings.  With a list `keep`, each training case's dense input volume
-    and target (for the convolutional comparison) are appended to it."""
+    and target (for the PyTorch comparison) are appended to it; with a UNet
+    `unet`, each steady state is added to it as a training volume."""
     import torch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -629,6 +633,8 @@ def train_warmstart_net(L, train, tol, args, keep=None):
     net = L.Net(width=704, depth=3, seed=1)
     for k in range(len(train)):
         net.add_sample(b, k)
+        if unet is not None:
+            unet.add_sample(b, k)
         if keep is not None:
             V = _dense_inputs(net, b, train[k], k)
             X = b.fields(k).astype(np.float32)
@@ -770,15 +776,38 @@ def main_warmstart(args, ws, rank, local):
     out = {"residual": tol, "test_shape": args.ws_test_shape, "train": {"64x32x32": args.ws_train,
                                                                        args.ws_test_shape: args.ws_train_test_shape}}
     kept = [] if args.ws_compare_unet else None
-    net, info = train_warmstart_net(L, train, tol, args, keep=kept)
+    unet = None
+    if args.ws_unet_iters > 0:
+        # one batch holds up to 8 volumes of one training grid; one test volume for the start
+        def vol(sh):
+            return int(np.prod([(d + 3) // 4 * 4 for d in sh]))
+        groups = {}
+        for c in train:
+            groups[c.solid.shape] = groups.get(c.solid.shape, 0) + 1
+        vmax = max([min(8, n) * vol(sh) for sh, n in groups.items()] + [vol(tshape)])
+        unet = L.UNet(width=args.ws_unet_width, max_voxels=vmax, seed=1)
+    net, info = train_warmstart_net(L, train, tol, args, keep=kept, unet=unet)
     out.update(info)
+    if unet is not None:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uloss = unet.train(args.ws_unet_iters, max_batch=8, lr=args.ws_lr)
+        torch.cuda.synchronize()
+        out["unet_training"] = {"params": unet.info()[0], "iters": args.ws_unet_iters, "max_batch": 8,
+                                "lr": args.ws_lr, "final_loss": uloss,
+                                "seconds": round(time.perf_counter() - t0, 2),
+                                "max_voxels": unet.max_voxels,
+                                "model": "3-D U-Net, 3 levels, widths %d/%d/%d, im2col + tcgen05 GEMMs of this "
+                                         "project" % (args.ws_unet_width, 2 * args.ws_unet_width,
+                                                      4 * args.ws_unet_width)}
     Wx = extrapolate_every_for(nx)
     forms = [("fp16_extrapolated", "fp16", Wx, 1)]
     if args.ws_plain:
         forms.insert(0, ("plain_fp32", "fp32", 0, 1))
     for label, prec, Wx, modes in forms:
         res = {"extrapolate_every": Wx, "extrapolate_modes": modes}
-        for start in ("uniform", "profile1d", "network"):
+        starts = ("uniform", "profile1d", "network") + (("unet",) if unet is not None else ())
+        for start in starts:
             bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx, extrapolate_modes=modes,
                                     init_mode="profile1d" if start == "profile1d" else "uniform")
             for k, c in enumerate(test):
@@ -790,6 +819,9 @@ def main_warmstart(args, ws, rank, local):
             if start == "network":
                 for k in range(len(test)):
                     net.warm_start(bt, k)
+            elif start == "unet":
+                for k in range(len(test)):
+                    unet.warm_start(bt, k)
             torch.cuda.synchronize()
             tb = time.perf_counter()
             n, steps, r, st = bt.run_to_residual(tol, args.max_steps, raise_on_fail=False)
@@ -800,17 +832,22 @@ def main_warmstart(args, ws, rank, local):
                           "batch_seconds": round(tc - tb, 2), "clocks": clocks.stop()}
             bt.close()
         if args.ws_compare_unet and label == "fp16_extrapolated":
-            res["unet"] = compare_unet(L, net, kept, test, tol, prec, Wx, modes, args)
-        for start in ("profile1d", "network", "unet"):
+            res["unet_pytorch"] = compare_unet(L, net, kept, test, tol, prec, Wx, modes, args)
+        for start in ("profile1d", "network", "unet", "unet_pytorch"):
             if start in res:
                 res[start]["steps_vs_uniform"] = round(res[start]["mean_steps"] / res["uniform"]["mean_steps"], 3)
         out[label] = res
     tc, ms = net.gemm_calls()
     out["gemm_calls"] = {"tcgen05": tc, "mma_sync": ms}
     net.close()
+    if unet is not None:
+        out["unet_gemm_calls"] = {"tcgen05": unet.gemm_calls()}
+        unet.close()
     if rank == 0:
-        v = out["fp16_extrapolated"]["network"]["mean_steps"]
-        line = {"metric": "steps to residual (held-out anodes, network start, FP16 + extrapolation)", "value": v,
+        chosen = "unet" if unet is not None else "network"
+        v = out["fp16_extrapolated"][chosen]["mean_steps"]
+        line = {"metric": "steps to residual (held-out anodes, %s start, FP16 + extrapolation)"
+                          % ("U-Net" if chosen == "unet" else "network"), "value": v,
                 "unit": "steps", "n_gpus": 1, "higher_is_better": False, "vs_baseline": None,
                 "dtype": "bf16 network, f32 LBM", "data": "synthetic",
                 "config": {"workload": f"learned warm start, {len(train)} training anodes "

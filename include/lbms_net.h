@@ -107,6 +107,74 @@ lbms_status lbms_net_gemm_calls(const lbms_net *net, int64_t *tcgen05_calls, int
 const char *lbms_net_last_error(const lbms_net *net);
 void lbms_net_destroy(lbms_net *net);
 
+/* ------------------------------------------------------------------------
+ * Convolutional warm start: a three-level 3-D U-Net over the anode's voxels
+ * (two 3x3x3 convolutions with zero padding and ReLU per level, 2x2x2 max
+ * pooling down, 2x2x2 stride-2 transposed convolutions up, skip
+ * concatenation, a 1x1 convolution to 3 outputs), with `width`, 2 width and
+ * 4 width channels on its levels.  Input channels: the 16 used feature
+ * columns of lbms_net_features on fluid voxels (zero on solid ones) and the
+ * fluid mask; output: 100 (X - X_profile), as the pointwise network.  Every
+ * convolution is an im2col and a BF16 matrix product on the tcgen05 tensor
+ * cores (FP32 accumulation); activations are stored BF16, weights BF16 with
+ * FP32 master copies (Adam, beta 0.9 / 0.999, eps 1e-8).
+ *
+ * A volume's extents must be multiples of 4 (the two poolings): a case is
+ * placed in a volume with its extents rounded up to multiples of 4, the
+ * added voxels solid (mask 0).  max_voxels bounds the voxels of one batch
+ * (B volumes; one volume for lbms_unet_warm_start), up to
+ * LBMS_UNET_MAX_VOXELS; the device memory held is about 6.5 kB per voxel of
+ * max_voxels.  width 4..32 (28 gives 1.05M parameters); weights He-uniform
+ * from a counter-based generator keyed by seed, head and biases zero. */
+typedef struct lbms_unet lbms_unet;
+
+enum { LBMS_UNET_MAX_VOXELS = 8000000 };   /* the padded rows stay within 65535 tiles of 128 */
+
+lbms_status lbms_unet_create(int width, int64_t max_voxels, uint64_t seed, lbms_unet **out);
+
+/* Adds one case of a handle as a training volume: its inputs and, as the
+ * target, 100 (X - X_profile) of the handle's current mole fractions on its
+ * fluid voxels (call it on a steady state).  The case must have boundary
+ * data and fit max_voxels. */
+lbms_status lbms_unet_add_sample(lbms_unet *net, lbms_ctx *ctx, int case_index);
+
+/* iters steps of Adam on the mean-square error over fluid voxels.  Step i
+ * takes the training volumes of group i mod G (volumes of equal extents, in
+ * order of first addition): min(max_batch, volumes in the group,
+ * max_voxels / voxels a volume) of them, drawn uniformly with replacement
+ * by a counter-based generator.  The learning rate decays from lr by a
+ * cosine to lr / 20 over the iterations of this call; last_loss (may be
+ * NULL) receives the mean loss of the last 10 steps. */
+lbms_status lbms_unet_train(lbms_unet *net, int iters, int max_batch, double lr, double *last_loss);
+
+/* Predicts the steady mole fractions of one case and restarts that case
+ * from them, as lbms_net_warm_start (clamped at 1e-6, renormalised; X may
+ * be NULL or receives the dense field [3][N]). */
+lbms_status lbms_unet_warm_start(lbms_unet *net, lbms_ctx *ctx, int case_index, double *X);
+
+/* Inference and one training step on caller-given volumes, for tests: x
+ * FP32 [B][17][Z][Y][X] (channel 16 the fluid mask), targets [B][3][Z][Y][X],
+ * out [B][3][Z][Y][X]; X, Y, Z multiples of 4.  The loss is
+ * sum((out - target)^2 mask) / (3 sum(mask)).  With lr = 0 the parameters
+ * do not change; the gradients are kept for lbms_unet_get. */
+lbms_status lbms_unet_forward(lbms_unet *net, const float *x, int B, int X, int Y, int Z, float *out);
+lbms_status lbms_unet_train_batch(lbms_unet *net, const float *x, const float *targets, int B, int X, int Y, int Z,
+                                  double lr, double *loss);
+
+/* Parameters (what = 0) or the gradients of the last step (what = 1) in
+ * the order and layouts of the PyTorch modules Conv3d / ConvTranspose3d:
+ * per layer (e1a, e1b, e2a, e2b, e3a, e3b, u2, d2a, d2b, u1, d1a, d1b, head)
+ * its weight ([co][ci][3][3][3]; transposed: [ci][co][2][2][2]; head
+ * [3][width]) then its bias [co].  n = floats the buffer holds. */
+lbms_status lbms_unet_get(const lbms_unet *net, int what, float *buf, int64_t n);
+lbms_status lbms_unet_set(lbms_unet *net, const float *params, int64_t n);
+
+lbms_status lbms_unet_info(const lbms_unet *net, int64_t *n_params, int64_t *n_samples);
+/* Matrix products computed on the tcgen05 tensor cores since creation. */
+lbms_status lbms_unet_gemm_calls(const lbms_unet *net, int64_t *tcgen05_calls);
+const char *lbms_unet_last_error(const lbms_unet *net);
+void lbms_unet_destroy(lbms_unet *net);
+
 #ifdef __cplusplus
 }
 #endif

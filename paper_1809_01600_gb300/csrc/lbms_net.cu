@@ -953,3 +953,5 @@ lbms_status lbms_net_warm_start(lbms_net* n, lbms_ctx* ctx, int k, double* Xout)
 }
 
 }  // extern "C"
+
+#include "lbms_unet.cuh"

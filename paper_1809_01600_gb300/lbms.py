@@ -20,6 +20,7 @@ LBMS_OK, LBMS_EINVAL, LBMS_ENOMEM, LBMS_ECUDA, LBMS_ENOTCONVERGED, LBMS_EUNSTABL
 LBMS_FP64, LBMS_FP32, LBMS_FP16 = 0, 1, 2
 LBMS_COUPLING_MS, LBMS_COUPLING_TAU_ONLY = 0, 1
 LBMS_INIT_UNIFORM, LBMS_INIT_PROFILE_1D = 0, 1
+UNET_MAX_VOXELS = 8000000
 _INIT_MODES = {"uniform": LBMS_INIT_UNIFORM, "profile1d": LBMS_INIT_PROFILE_1D}
 LBMS_OUTLET_FLUX, LBMS_OUTLET_EXTRAPOLATED = 0, 1
 LBMS_GRAD_CENTRAL, LBMS_GRAD_FORWARD = 0, 1
@@ -40,6 +41,9 @@ NET_EXPORTS = ("lbms_net_create", "lbms_net_add_sample", "lbms_net_features", "l
                "lbms_net_warm_start", "lbms_net_set_gemm", "lbms_net_gemm_calls",
                "lbms_net_forward", "lbms_net_train_batch", "lbms_net_get", "lbms_net_set", "lbms_net_info",
                "lbms_net_last_error", "lbms_net_destroy")
+UNET_EXPORTS = ("lbms_unet_create", "lbms_unet_add_sample", "lbms_unet_train", "lbms_unet_warm_start",
+                "lbms_unet_forward", "lbms_unet_train_batch", "lbms_unet_get", "lbms_unet_set", "lbms_unet_info",
+                "lbms_unet_gemm_calls", "lbms_unet_last_error", "lbms_unet_destroy")
 
 
 class LbmsError(RuntimeError):
@@ -146,6 +150,18 @@ def load(build_if_needed: bool = True):
         "lbms_net_info": (st, [P, C.POINTER(I64), C.POINTER(I64)]),
         "lbms_net_last_error": (C.c_char_p, [P]),
         "lbms_net_destroy": (None, [P]),
+        "lbms_unet_create": (st, [C.c_int, I64, C.c_uint64, C.POINTER(P)]),
+        "lbms_unet_add_sample": (st, [P, P, C.c_int]),
+        "lbms_unet_train": (st, [P, C.c_int, C.c_int, C.c_double, D]),
+        "lbms_unet_warm_start": (st, [P, P, C.c_int, D]),
+        "lbms_unet_forward": (st, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]),
+        "lbms_unet_train_batch": (st, [P, P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, D]),
+        "lbms_unet_get": (st, [P, C.c_int, P, I64]),
+        "lbms_unet_set": (st, [P, P, I64]),
+        "lbms_unet_info": (st, [P, C.POINTER(I64), C.POINTER(I64)]),
+        "lbms_unet_gemm_calls": (st, [P, C.POINTER(I64)]),
+        "lbms_unet_last_error": (C.c_char_p, [P]),
+        "lbms_unet_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -568,6 +584,106 @@ class Net:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.lbms_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class UNet:
+    """The convolutional warm start of include/lbms_net.h (argument marshalling only)."""
+
+    IN_CHANNELS = 17
+
+    def __init__(self, width=28, max_voxels=1 << 20, seed=0):
+        self._lib = load()
+        h = C.c_void_p()
+        s = self._lib.lbms_unet_create(int(width), int(max_voxels), int(seed), C.byref(h))
+        if s != LBMS_OK:
+            raise LbmsError(s, "lbms_unet_create(width=%d, max_voxels=%d)" % (width, max_voxels))
+        self._h = h
+        self.width, self.max_voxels = width, max_voxels
+
+    def _check(self, s):
+        if s != LBMS_OK:
+            raise LbmsError(s, self._lib.lbms_unet_last_error(self._h).decode())
+
+    def info(self):
+        a, b = C.c_int64(), C.c_int64()
+        self._check(self._lib.lbms_unet_info(self._h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def gemm_calls(self):
+        a = C.c_int64()
+        self._check(self._lib.lbms_unet_gemm_calls(self._h, C.byref(a)))
+        return a.value
+
+    def add_sample(self, handle, case=0):
+        self._check(self._lib.lbms_unet_add_sample(self._h, handle._h, int(case)))
+
+    def train(self, iters, max_batch=8, lr=1e-3):
+        loss = C.c_double()
+        self._check(self._lib.lbms_unet_train(self._h, int(iters), int(max_batch), float(lr), C.byref(loss)))
+        return loss.value
+
+    def warm_start(self, handle, case=0):
+        shape = handle.shapes[case] if hasattr(handle, "shapes") else handle.shape
+        X = np.empty((3,) + tuple(shape))
+        self._check(self._lib.lbms_unet_warm_start(self._h, handle._h, int(case), _dptr(X)))
+        return X
+
+    def forward(self, x):
+        """x float32 [B, 17, Z, Y, X] -> [B, 3, Z, Y, X]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        B, _, Z, Y, X = x.shape
+        out = np.empty((B, 3, Z, Y, X), dtype=np.float32)
+        self._check(self._lib.lbms_unet_forward(self._h, x.ctypes.data, B, X, Y, Z, out.ctypes.data))
+        return out
+
+    def train_batch(self, x, targets, lr=0.0):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        B, _, Z, Y, X = x.shape
+        loss = C.c_double()
+        self._check(self._lib.lbms_unet_train_batch(self._h, x.ctypes.data, t.ctypes.data, B, X, Y, Z, float(lr),
+                                                    C.byref(loss)))
+        return loss.value
+
+    def shapes(self):
+        """Parameter shapes in order (those of the equivalent PyTorch modules)."""
+        w = self.width
+        out = []
+        for ci, co in ((17, w), (w, w), (w, 2 * w), (2 * w, 2 * w), (2 * w, 4 * w), (4 * w, 4 * w)):
+            out += [(co, ci, 3, 3, 3), (co,)]
+        out += [(4 * w, 2 * w, 2, 2, 2), (2 * w,)]
+        out += [(2 * w, 4 * w, 3, 3, 3), (2 * w,), (2 * w, 2 * w, 3, 3, 3), (2 * w,)]
+        out += [(2 * w, w, 2, 2, 2), (w,)]
+        out += [(w, 2 * w, 3, 3, 3), (w,), (w, w, 3, 3, 3), (w,)]
+        out += [(3, w, 1, 1, 1), (3,)]
+        return out
+
+    def get(self, what=0):
+        """Parameters (0) or last gradients (1) as a list of arrays of shapes()."""
+        n, _ = self.info()
+        buf = np.empty(n, dtype=np.float32)
+        self._check(self._lib.lbms_unet_get(self._h, int(what), buf.ctypes.data, n))
+        out, off = [], 0
+        for sh in self.shapes():
+            k = int(np.prod(sh))
+            out.append(buf[off:off + k].reshape(sh))
+            off += k
+        return out
+
+    def set(self, params):
+        flat = np.concatenate([np.asarray(p, dtype=np.float32).ravel() for p in params])
+        self._check(self._lib.lbms_unet_set(self._h, flat.ctypes.data, flat.size))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.lbms_unet_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -34,7 +34,17 @@ def test_every_network_symbol_is_exported():
     names = declared_functions(NET_HEADER)
     for n in names:
         assert hasattr(lib, n), n
-    assert set(names) == set(L.NET_EXPORTS)
+    assert set(names) == set(L.NET_EXPORTS) | set(L.UNET_EXPORTS)
+
+
+def test_unet_create_rejects_bad_sizes_without_a_gpu():
+    """Width and voxel bounds are checked before any CUDA call."""
+    lib = L.load()
+    h = C.c_void_p()
+    for width, vox in ((3, 4096), (33, 4096), (28, 63), (28, L.UNET_MAX_VOXELS + 1)):
+        assert lib.lbms_unet_create(width, vox, 0, C.byref(h)) == L.LBMS_EINVAL
+        assert not h.value
+    assert lib.lbms_unet_create(28, 4096, 0, None) == L.LBMS_EINVAL
 
 
 def test_bf16_conversion_round_trip():
