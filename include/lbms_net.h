@@ -115,17 +115,20 @@ void lbms_net_destroy(lbms_net *net);
  * 4 width channels on its levels.  Input channels: the 16 used feature
  * columns of lbms_net_features on fluid voxels (zero on solid ones) and the
  * fluid mask; output: 100 (X - X_profile), as the pointwise network.  Every
- * convolution is an im2col and a BF16 matrix product on the tcgen05 tensor
- * cores (FP32 accumulation); activations are stored BF16, weights BF16 with
- * FP32 master copies (Adam, beta 0.9 / 0.999, eps 1e-8).
+ * convolution is an implicit GEMM on the tcgen05 tensor cores (BF16
+ * operands staged by TMA, FP32 accumulation): activations are stored BF16
+ * with a zero halo around each volume, so each tap reads the activation
+ * matrix at a shifted row; weights are BF16 with FP32 master copies (Adam,
+ * beta 0.9 / 0.999, eps 1e-8).
  *
  * A volume's extents must be multiples of 4 (the two poolings): a case is
  * placed in a volume with its extents rounded up to multiples of 4, the
  * added voxels solid (mask 0).  max_voxels bounds the voxels of one batch
  * (B volumes; one volume for lbms_unet_warm_start), up to
- * LBMS_UNET_MAX_VOXELS; the device memory held is about 6.5 kB per voxel of
- * max_voxels.  width 4..32 (28 gives 1.05M parameters); weights He-uniform
- * from a counter-based generator keyed by seed, head and biases zero. */
+ * LBMS_UNET_MAX_VOXELS.  Activation buffers are allocated for the largest
+ * batch met, about 3.4 kB per voxel of it (8 volumes of 96^3: 27 GB).
+ * width 4..32 (28 gives 1.05M parameters); weights He-uniform from a
+ * counter-based generator keyed by seed, head and biases zero. */
 typedef struct lbms_unet lbms_unet;
 
 enum { LBMS_UNET_MAX_VOXELS = 8000000 };   /* the padded rows stay within 65535 tiles of 128 */

@@ -12,6 +12,19 @@
 // store FP32.  Rows and K beyond the operands' extents are zero-filled by
 // TMA, so M and K need no padding; N is a multiple of 64.
 //
+// Two more load modes turn the same kernel into the convolutions of the
+// 3-D U-Net (lbms_unet.cuh), whose activations are stored in a layout with a
+// zero halo of one voxel per side, so that the neighbour of every interior
+// voxel at tap t = (dz, dy, dx) lies a fixed number of rows off(t) away:
+//  * implicit convolution (mode 1): K runs over 27 taps x C channels; the
+//    A tile of tap t is the activation matrix [rows][C] read at rows
+//    m0 + off(t) (TMA zero-fills rows outside it), B the weights [N][27 C];
+//  * weight gradient (mode 2): P[m][t C + c] = sum_r A[m][r] x[r + off(t)][c]
+//    with A = dZ^T [M][rows]; B comes from one of three transposed copies
+//    xT_j[c][r] = x[r + j - 1][c] (j = dx + 1), read at inner coordinate
+//    r + (dz Yp + dy) Xp, a multiple of 8 elements when the padded x extent
+//    Xp is (the 16-byte rule of tiled TMA).
+//
 // Every mbarrier wait is bounded (about 2 s on the global timer): on a
 // timeout the kernel raises *err, still waits (bounded) for the copies it
 // issued, frees its TMEM and returns.
@@ -120,10 +133,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr));
 }
 
+// Load modes of the kernel (see the head of the file).
+constexpr int kModePlain = 0, kModeConv = 1, kModeWgrad = 2;
+
+template <int kMode>
 __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
                                                            const __grid_constant__ CUtensorMap mapB,
+                                                           const __grid_constant__ CUtensorMap mapB1,
+                                                           const __grid_constant__ CUtensorMap mapB2,
                                                            float* __restrict__ P, int M, int N, int kchunk,
-                                                           unsigned int* __restrict__ err) {
+                                                           unsigned int* __restrict__ err, const __grid_constant__ ConvTaps taps) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kStages * kStageBytes);
@@ -156,12 +175,25 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
     if (threadIdx.x == 0) {
         bool ok = true;
         int issued = 0;                        // stages whose loads were issued
+        // mode 2: the tap of this CTA's 64 output columns picks the copy and the shift of B
+        const int wtap = kMode == kModeWgrad ? n0 / taps.per_tap : 0;
+        const CUtensorMap* mb = &mapB;
+        if (kMode == kModeWgrad) mb = wtap % 3 == 0 ? &mapB : wtap % 3 == 1 ? &mapB1 : &mapB2;
         auto load = [&](int kt) {
             const int s = kt % kStages;
             uint8_t* sa = base + (size_t)s * kStageBytes;
             mbar_expect_tx(&full[s], kStageBytes);
-            tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
-            tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
+            if (kMode == kModeConv) {
+                const int t = kt / taps.per_tap, c = kt - t * taps.per_tap;
+                tma_load_2d(sa, &mapA, c * kUK, m0 + taps.off[t], &full[s]);
+                tma_load_2d(sa + kABytes, &mapB, kt * kUK, n0, &full[s]);
+            } else if (kMode == kModeWgrad) {
+                tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
+                tma_load_2d(sa + kABytes, mb, k0 + kt * kUK + taps.off[wtap], n0 - wtap * taps.per_tap, &full[s]);
+            } else {
+                tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
+                tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
+            }
             ++issued;
         };
         for (int kt = 0; kt < nk && kt < kStages; ++kt) load(kt);
@@ -240,7 +272,14 @@ void init_once() {
         return;
     }
     g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    g_init = cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModePlain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemBytes);
+    if (g_init == cudaSuccess)
+        g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModeConv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmemBytes);
+    if (g_init == cudaSuccess)
+        g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModeWgrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSmemBytes);
 }
 
 // 2-D tensor map of a K-contiguous BF16 operand: inner extent K, `rows`
@@ -278,7 +317,41 @@ cudaError_t umma_gemm_tn(const void* A, int lda, const void* B, int ldb, float* 
     CUtensorMap ma, mb;
     if (!make_map(&ma, A, K, M, lda, kUM) || !make_map(&mb, B, K, N, ldb, kUN)) return cudaErrorInvalidValue;
     const dim3 grid(N / kUN, (M + kUM - 1) / kUM, S);
-    umma_gemm_kernel<<<grid, 128, kSmemBytes, st>>>(ma, mb, P, M, N, K / S, err);
+    umma_gemm_kernel<kModePlain><<<grid, 128, kSmemBytes, st>>>(ma, mb, mb, mb, P, M, N, K / S, err, ConvTaps{});
+    return cudaGetLastError();
+}
+
+cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N, const ConvTaps& taps, float* P,
+                           unsigned int* err, cudaStream_t st) {
+    cudaError_t e = umma_gemm_init();
+    if (e != cudaSuccess) return e;
+    if (rows < 1 || C < kUK || C % kUK || N < kUN || N % kUN || taps.per_tap != C / kUK ||
+        (rows + kUM - 1) / kUM > 65535 || ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(W)) & 15u))
+        return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, x, C, rows, C, kUM) || !make_map(&mb, W, 27 * C, N, 27 * C, kUN)) return cudaErrorInvalidValue;
+    const dim3 grid(N / kUN, (rows + kUM - 1) / kUM, 1);
+    umma_gemm_kernel<kModeConv><<<grid, 128, kSmemBytes, st>>>(ma, mb, mb, mb, P, rows, N, 27 * C, err, taps);
+    return cudaGetLastError();
+}
+
+cudaError_t umma_wgrad_gemm(const void* dzT, int M, const void* const xT[3], int C, int rows, int S,
+                            const ConvTaps& taps, float* P, unsigned int* err, cudaStream_t st) {
+    cudaError_t e = umma_gemm_init();
+    if (e != cudaSuccess) return e;
+    uintptr_t al = reinterpret_cast<uintptr_t>(dzT);
+    for (int j = 0; j < 3; ++j) al |= reinterpret_cast<uintptr_t>(xT[j]);
+    bool ok = M >= 1 && M <= kUM && C >= kUN && C % kUN == 0 && rows >= kUK && rows % 8 == 0 && S >= 1 &&
+              rows % S == 0 && (rows / S) % kUK == 0 && taps.per_tap == C && S <= 65535 && !(al & 15u);
+    for (int t = 0; t < 27 && ok; ++t) ok = taps.off[t] % 8 == 0;
+    if (!ok) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb[3];
+    if (!make_map(&ma, dzT, rows, M, rows, kUM)) return cudaErrorInvalidValue;
+    for (int j = 0; j < 3; ++j)
+        if (!make_map(&mb[j], xT[j], rows, C, rows, kUN)) return cudaErrorInvalidValue;
+    const dim3 grid(27 * C / kUN, 1, S);
+    umma_gemm_kernel<kModeWgrad><<<grid, 128, kSmemBytes, st>>>(ma, mb[0], mb[1], mb[2], P, M, 27 * C, rows / S, err,
+                                                                taps);
     return cudaGetLastError();
 }
 
