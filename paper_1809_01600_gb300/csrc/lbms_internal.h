@@ -136,17 +136,17 @@ cudaError_t umma_gemm_tn(const void* A, int lda, const void* B, int ldb, float* 
 // t = 9 (dz + 1) + 3 (dy + 1) + (dx + 1) a row offset in the zero-halo layout
 // of the activations.  umma_conv_gemm: P[r][n] = sum_t sum_c x[r + off[t]][c]
 // W[n][t C + c] over rows r of x [rows][C] (C = 64 per_tap), W [N][27 C].
-// umma_wgrad_gemm: P[z][m][t C + c] = sum_{r in chunk z} dzT[m][r]
-// xT[t % 3][c][r + off[t]] with dzT [M <= 128][rows], xT[j] [C][rows]
-// (per_tap = C, each off a multiple of 8).  Both read zeros outside their
-// operands' extents.
+// umma_wgrad_gemm: P[z][t C + c][n] = sum_{r in chunk z}
+// xT[t % 3][c][r + off[t]] dzT[n][r] with xT[j] [C][rows], dzT [N][rows]
+// (per_tap = C, a multiple of 64; N a multiple of 64; each off a multiple of
+// 8).  Both read zeros outside their operands' extents.
 struct ConvTaps {
     int per_tap = 1;
     int off[27] = {};
 };
 cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N, const ConvTaps& taps, float* P,
                            unsigned int* err, cudaStream_t st);
-cudaError_t umma_wgrad_gemm(const void* dzT, int M, const void* const xT[3], int C, int rows, int S,
+cudaError_t umma_wgrad_gemm(const void* dzT, int N, const void* const xT[3], int C, int rows, int S,
                             const ConvTaps& taps, float* P, unsigned int* err, cudaStream_t st);
 
 // Read-only view of one case of a handle (for the warm-start network).

@@ -19,11 +19,12 @@
 //  * implicit convolution (mode 1): K runs over 27 taps x C channels; the
 //    A tile of tap t is the activation matrix [rows][C] read at rows
 //    m0 + off(t) (TMA zero-fills rows outside it), B the weights [N][27 C];
-//  * weight gradient (mode 2): P[m][t C + c] = sum_r A[m][r] x[r + off(t)][c]
-//    with A = dZ^T [M][rows]; B comes from one of three transposed copies
-//    xT_j[c][r] = x[r + j - 1][c] (j = dx + 1), read at inner coordinate
-//    r + (dz Yp + dy) Xp, a multiple of 8 elements when the padded x extent
-//    Xp is (the 16-byte rule of tiled TMA).
+//  * weight gradient (mode 2): P[t C + c][n] = sum_r x[r + off(t)][c] dZ[r][n]
+//    with B = dZ^T [N][rows]; the A tile's two 64-row halves come from three
+//    transposed copies xT_j[c][r] = x[r + j - 1][c] (j = dx + 1) of the
+//    input, each read at inner coordinate r + (dz Yp + dy) Xp, a multiple of
+//    8 elements when the padded x extent Xp is (the 16-byte rule of tiled
+//    TMA); rows of A past 27 C read as zero.
 //
 // Every mbarrier wait is bounded (about 2 s on the global timer): on a
 // timeout the kernel raises *err, still waits (bounded) for the copies it
@@ -175,10 +176,22 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
     if (threadIdx.x == 0) {
         bool ok = true;
         int issued = 0;                        // stages whose loads were issued
-        // mode 2: the tap of this CTA's 64 output columns picks the copy and the shift of B
-        const int wtap = kMode == kModeWgrad ? n0 / taps.per_tap : 0;
-        const CUtensorMap* mb = &mapB;
-        if (kMode == kModeWgrad) mb = wtap % 3 == 0 ? &mapB : wtap % 3 == 1 ? &mapB1 : &mapB2;
+        // mode 2: each 64-row half h of the A tile is one tap's channel block:
+        // its copy (by dx), its inner shift and its first channel
+        const CUtensorMap* ma2[2] = {&mapA, &mapA};
+        int shift2[2] = {0, 0}, c2[2] = {0, 0};
+        if (kMode == kModeWgrad) {
+            for (int h = 0; h < 2; ++h) {
+                const int m = m0 + 64 * h, t = m / taps.per_tap;
+                if (t < 27) {
+                    ma2[h] = t % 3 == 0 ? &mapA : t % 3 == 1 ? &mapB1 : &mapB2;
+                    shift2[h] = taps.off[t];
+                    c2[h] = m - t * taps.per_tap;
+                } else {
+                    c2[h] = taps.per_tap;   // past the copy's rows: zero-filled
+                }
+            }
+        }
         auto load = [&](int kt) {
             const int s = kt % kStages;
             uint8_t* sa = base + (size_t)s * kStageBytes;
@@ -188,8 +201,9 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
                 tma_load_2d(sa, &mapA, c * kUK, m0 + taps.off[t], &full[s]);
                 tma_load_2d(sa + kABytes, &mapB, kt * kUK, n0, &full[s]);
             } else if (kMode == kModeWgrad) {
-                tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
-                tma_load_2d(sa + kABytes, mb, k0 + kt * kUK + taps.off[wtap], n0 - wtap * taps.per_tap, &full[s]);
+                tma_load_2d(sa, ma2[0], k0 + kt * kUK + shift2[0], c2[0], &full[s]);
+                tma_load_2d(sa + kABytes / 2, ma2[1], k0 + kt * kUK + shift2[1], c2[1], &full[s]);
+                tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
             } else {
                 tma_load_2d(sa, &mapA, k0 + kt * kUK, m0, &full[s]);
                 tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
@@ -335,22 +349,23 @@ cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N,
     return cudaGetLastError();
 }
 
-cudaError_t umma_wgrad_gemm(const void* dzT, int M, const void* const xT[3], int C, int rows, int S,
+cudaError_t umma_wgrad_gemm(const void* dzT, int N, const void* const xT[3], int C, int rows, int S,
                             const ConvTaps& taps, float* P, unsigned int* err, cudaStream_t st) {
     cudaError_t e = umma_gemm_init();
     if (e != cudaSuccess) return e;
     uintptr_t al = reinterpret_cast<uintptr_t>(dzT);
     for (int j = 0; j < 3; ++j) al |= reinterpret_cast<uintptr_t>(xT[j]);
-    bool ok = M >= 1 && M <= kUM && C >= kUN && C % kUN == 0 && rows >= kUK && rows % 8 == 0 && S >= 1 &&
+    bool ok = N >= kUN && N % kUN == 0 && C >= 64 && C % 64 == 0 && rows >= kUK && rows % 8 == 0 && S >= 1 &&
               rows % S == 0 && (rows / S) % kUK == 0 && taps.per_tap == C && S <= 65535 && !(al & 15u);
     for (int t = 0; t < 27 && ok; ++t) ok = taps.off[t] % 8 == 0;
     if (!ok) return cudaErrorInvalidValue;
-    CUtensorMap ma, mb[3];
-    if (!make_map(&ma, dzT, rows, M, rows, kUM)) return cudaErrorInvalidValue;
+    CUtensorMap ma[3], mb;
     for (int j = 0; j < 3; ++j)
-        if (!make_map(&mb[j], xT[j], rows, C, rows, kUN)) return cudaErrorInvalidValue;
-    const dim3 grid(27 * C / kUN, 1, S);
-    umma_gemm_kernel<kModeWgrad><<<grid, 128, kSmemBytes, st>>>(ma, mb[0], mb[1], mb[2], P, M, 27 * C, rows / S, err,
+        if (!make_map(&ma[j], xT[j], rows, C, rows, kUM / 2)) return cudaErrorInvalidValue;
+    if (!make_map(&mb, dzT, rows, N, rows, kUN)) return cudaErrorInvalidValue;
+    const int M = 27 * C;
+    const dim3 grid(N / kUN, (M + kUM - 1) / kUM, S);
+    umma_gemm_kernel<kModeWgrad><<<grid, 128, kSmemBytes, st>>>(ma[0], mb, ma[1], ma[2], P, M, N, rows / S, err,
                                                                 taps);
     return cudaGetLastError();
 }

@@ -198,19 +198,75 @@ __global__ void colsum_kernel(const float* __restrict__ d, int64_t R, int C, flo
     }
 }
 
-// out[c][r] = in[r + shift][c] (0 where r + shift is outside [0, R)); R and C
-// multiples of 32, 32 x 32 tiles through shared memory, rows on grid x.
-__global__ void transpose_shift_kernel(const bf16* __restrict__ in, bf16* __restrict__ out, int64_t R, int C,
-                                       int shift) {
-    __shared__ bf16 tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int c0 = blockIdx.y * 32;
-    for (int y = threadIdx.y; y < 32; y += 8) {
-        const int64_t rs = r0 + y + shift;
-        tile[y][threadIdx.x] = rs >= 0 && rs < R ? in[rs * C + c0 + threadIdx.x] : __float2bfloat16_rn(0.0f);
+// ncopy transposed copies of in [R][C]: out[j][c][r] = in[r + j + shift0][c]
+// (0 where that row is outside [0, R)); R and C multiples of 64.  A block of
+// 256 threads reads 64 + ncopy - 1 rows x 64 channels once (16-byte loads)
+// and writes the 64 x 64 tiles of every copy (16-byte stores, 8 threads per
+// 128-byte output row).  The shared tile's rows are 33 words apart, so the
+// 8 rows a warp reads at once fall in 2 ways of the banks.
+__global__ void __launch_bounds__(256) transpose_copies_kernel(const bf16* __restrict__ in, bf16* __restrict__ out,
+                                                               int64_t R, int C, int ncopy, int shift0) {
+    __shared__ __align__(16) bf16 tile[66][66];
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int c0 = blockIdx.y * 64;
+    const int nrows = 64 + ncopy - 1;
+    for (int e = threadIdx.x; e < nrows * 8; e += 256) {
+        const int i = e >> 3, q = (e & 7) * 8;
+        const int64_t rs = r0 + i + shift0;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (rs >= 0 && rs < R) v = *reinterpret_cast<const uint4*>(in + rs * C + c0 + q);
+        uint32_t* d = reinterpret_cast<uint32_t*>(&tile[i][q]);
+        d[0] = v.x;
+        d[1] = v.y;
+        d[2] = v.z;
+        d[3] = v.w;
     }
     __syncthreads();
-    for (int y = threadIdx.y; y < 32; y += 8) out[(int64_t)(c0 + y) * R + r0 + threadIdx.x] = tile[threadIdx.x][y];
+    for (int j = 0; j < ncopy; ++j) {
+        bf16* o = out + (size_t)j * C * R;
+        for (int e = threadIdx.x; e < 64 * 8; e += 256) {
+            const int c = e >> 3, q = (e & 7) * 8;
+            __align__(16) bf16 v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = tile[q + k + j][c];
+            *reinterpret_cast<uint4*>(o + (int64_t)(c0 + c) * R + r0 + q) = *reinterpret_cast<const uint4*>(v);
+        }
+    }
+}
+
+// dZ = dA * (act > 0) as BF16 [R][C] (C 64 or 128) and the column sums of
+// dZ added into gb; a block of 256 threads per 64 rows.
+__global__ void __launch_bounds__(256) relu_back_rows_kernel(const float* __restrict__ dA, const bf16* __restrict__ act,
+                                                             int64_t R, int C, bf16* __restrict__ dZ,
+                                                             float* __restrict__ gb) {
+    __shared__ float part[256];
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    const int c = threadIdx.x % C, g = threadIdx.x / C, ng = 256 / C;
+    float s = 0.0f;
+    for (int64_t r = r0 + g; r < r0 + 64 && r < R; r += ng) {
+        const int64_t e = r * C + c;
+        const float v = __bfloat162float(act[e]) > 0.0f ? dA[e] : 0.0f;
+        dZ[e] = __float2bfloat16_rn(v);
+        s += v;
+    }
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x < C) {
+        float t = 0.0f;
+        for (int k = 0; k < ng; ++k) t += part[k * C + threadIdx.x];
+        atomicAdd(&gb[threadIdx.x], t);
+    }
+}
+
+// G[o][i] = sum_z P[z][i][o] (split-K partials of a transposed product).
+__global__ void splitk_sum_t_kernel(const float* __restrict__ P, int S, int I, int O, float* __restrict__ G) {
+    const int64_t n = (int64_t)O * I;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const int o = (int)(e / I), i = (int)(e % I);
+        float acc = 0.0f;
+        for (int z = 0; z < S; ++z) acc += P[(int64_t)z * n + (int64_t)i * O + o];
+        G[e] = acc;
+    }
 }
 
 // BF16 copies of a 3x3x3 convolution's FP32 weights W [co_s][27 ci_s]
@@ -564,10 +620,12 @@ lbms_status ugemm(lbms_unet* u, const bf16* A, int64_t lda, const bf16* B, int64
     return LBMS_OK;
 }
 
-// out[c][r] = in[r + shift][c] over R rows (zero outside).
-lbms_status transpose_rows(lbms_unet* u, const bf16* in, bf16* out, int64_t R, int C, int shift, size_t cap) {
-    if ((size_t)R * C > cap) return ufail(u, LBMS_EINVAL, "U-Net transpose %lld x %d too large", (long long)R, C);
-    transpose_shift_kernel<<<dim3((unsigned)(R / 32), C / 32), dim3(32, 8)>>>(in, out, R, C, shift);
+// ncopy transposed copies out[j][c][r] = in[r + j + shift0][c] over R rows (zero outside).
+lbms_status transpose_rows(lbms_unet* u, const bf16* in, bf16* out, int64_t R, int C, int ncopy, int shift0,
+                           size_t cap) {
+    if ((size_t)ncopy * R * C > cap || R % 64 || C % 64)
+        return ufail(u, LBMS_EINVAL, "U-Net transpose %lld x %d not supported", (long long)R, C);
+    transpose_copies_kernel<<<dim3((unsigned)(R / 64), C / 64), 256>>>(in, out, R, C, ncopy, shift0);
     UCK(cudaGetLastError(), "transpose");
     return LBMS_OK;
 }
@@ -611,22 +669,18 @@ lbms_status up_fwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const
 // [Rp][ci_s] (zero outside the volumes).
 lbms_status conv_bwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const bf16* a, const float* dA,
                      const Geo& g, float* dx) {
-    relu_back_kernel<<<(unsigned)(g.Rp / 32), 256>>>(dA, a, (int)g.Rp, l.co_s, u->dz, l.gb);
+    relu_back_rows_kernel<<<(unsigned)(g.Rp / 64), 256>>>(dA, a, g.Rp, l.co_s, u->dz, l.gb);
     UCK(cudaGetLastError(), "relu backward");
-    UST(transpose_rows(u, u->dz, u->dzT, g.Rp, l.co_s, 0, u->g_elems));
-    const bf16* xT[3];
-    for (int j = 0; j < 3; ++j) {
-        bf16* dst = u->xT + (size_t)j * l.ci_s * g.Rp;
-        UST(transpose_rows(u, x, dst, g.Rp, l.ci_s, j - 1, u->xT_elems / 3));
-        xT[j] = dst;
-    }
+    UST(transpose_rows(u, u->dz, u->dzT, g.Rp, l.co_s, 1, 0, u->g_elems));
+    UST(transpose_rows(u, x, u->xT, g.Rp, l.ci_s, 3, -1, u->xT_elems));
+    const void* xT[3];
+    for (int j = 0; j < 3; ++j) xT[j] = u->xT + (size_t)j * l.ci_s * g.Rp;
     if ((size_t)g.S * l.co_s * l.K > u->P_floats) return ufail(u, LBMS_EINVAL, "U-Net weight gradient too large");
     const lbms::ConvTaps tw = wgrad_taps(g, l.ci_s);
-    UCK(lbms::umma_wgrad_gemm(u->dzT, l.co_s, reinterpret_cast<const void* const*>(xT), l.ci_s, (int)g.Rp, g.S, tw,
-                              u->P, u->gemm_err, 0),
+    UCK(lbms::umma_wgrad_gemm(u->dzT, l.co_s, xT, l.ci_s, (int)g.Rp, g.S, tw, u->P, u->gemm_err, 0),
         "weight gradient");
     ++u->tcgen05_calls;
-    splitk_sum_kernel<<<grid_for((int64_t)l.co_s * l.K), 256>>>(u->P, g.S, (int64_t)l.co_s * l.K, l.g);
+    splitk_sum_t_kernel<<<grid_for((int64_t)l.co_s * l.K), 256>>>(u->P, g.S, l.K, l.co_s, l.g);
     UCK(cudaGetLastError(), "split-k sum");
     if (!dx) return LBMS_OK;
     if ((size_t)g.Rp * l.ci_s > u->P_floats) return ufail(u, LBMS_EINVAL, "U-Net input gradient too large");
@@ -645,8 +699,8 @@ lbms_status up_bwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const
     if ((size_t)lo.Rp * l.rows > u->g_elems) return ufail(u, LBMS_EINVAL, "U-Net gather too large");
     upgather_rows_kernel<<<warp_grid(lo.Rp), 256>>>(dy, lo, hi, l.co_s, u->G);
     UCK(cudaGetLastError(), "up gather");
-    UST(transpose_rows(u, u->G, u->dzT, lo.Rp, l.rows, 0, u->g_elems));
-    UST(transpose_rows(u, x, u->aT, lo.Rp, l.ci_s, 0, u->g_elems));
+    UST(transpose_rows(u, u->G, u->dzT, lo.Rp, l.rows, 1, 0, u->g_elems));
+    UST(transpose_rows(u, x, u->aT, lo.Rp, l.ci_s, 1, 0, u->g_elems));
     UST(ugemm(u, u->dzT, lo.Rp, u->aT, lo.Rp, l.rows, l.ci_s, lo.Rp, lo.S));
     splitk_sum_kernel<<<grid_for((int64_t)l.rows * l.K), 256>>>(u->P, lo.S, (int64_t)l.rows * l.K, l.g);
     UCK(cudaGetLastError(), "split-k sum");
@@ -696,8 +750,8 @@ lbms_status unet_backward(lbms_unet* u, const Levels& v, float inv_n) {
     const lbms_unet::Layer& h = L[12];
     unet_loss_kernel<<<(unsigned)(g0.Rp / 64), 256>>>(u->P, h.b, u->T, g0.Rp, inv_n, u->dz, h.gb, u->loss, u->Y);
     UCK(cudaGetLastError(), "loss");
-    UST(transpose_rows(u, u->dz, u->dzT, g0.Rp, kUOutC, 0, u->g_elems));
-    UST(transpose_rows(u, u->d1, u->aT, g0.Rp, h.ci_s, 0, u->g_elems));
+    UST(transpose_rows(u, u->dz, u->dzT, g0.Rp, kUOutC, 1, 0, u->g_elems));
+    UST(transpose_rows(u, u->d1, u->aT, g0.Rp, h.ci_s, 1, 0, u->g_elems));
     UST(ugemm(u, u->dzT, g0.Rp, u->aT, g0.Rp, h.rows, h.ci_s, g0.Rp, g0.S));
     splitk_sum_kernel<<<grid_for((int64_t)h.rows * h.K), 256>>>(u->P, g0.S, (int64_t)h.rows * h.K, h.g);
     UCK(cudaGetLastError(), "split-k sum");
