@@ -37,6 +37,7 @@ WORKLOADS = {
     "sweep": None,
     "table2": None,
     "warmstart": None,
+    "unet": None,
 }
 METRIC = "MLUPS/species"
 
@@ -107,6 +108,12 @@ def parse():
     ap.add_argument("--ws-unet-iters", type=int, default=6000,
                     help="warm start: Adam steps of the 3-D U-Net on this project's kernels (0 skips it)")
     ap.add_argument("--ws-unet-width", type=int, default=28, help="warm start: U-Net width (28: 1.05M parameters)")
+    ap.add_argument("--unet-shape", default="96x96x96", help="--workload unet: volume grid (nx x ny x nz)")
+    ap.add_argument("--unet-batch", type=int, default=8, help="--workload unet: volumes per training step")
+    ap.add_argument("--unet-steps", type=int, default=20, help="--workload unet: timed training steps")
+    ap.add_argument("--unet-torch", action="store_true",
+                    help="--workload unet: also time the same U-Net with PyTorch convolutions (TF32 and BF16 "
+                         "autocast) on the same volumes")
     return ap.parse_args()
 
 
@@ -456,6 +463,8 @@ def main():
         return main_table2(args, ws, rank, local)
     if args.workload == "warmstart":
         return main_warmstart(args, ws, rank, local)
+    if args.workload == "unet":
+        return main_unet(args, ws, rank, local)
 
     import torch
     if not torch.cuda.is_available():
@@ -797,7 +806,7 @@ def main_warmstart(args, ws, rank, local):
                                 "lr": args.ws_lr, "final_loss": uloss,
                                 "seconds": round(time.perf_counter() - t0, 2),
                                 "max_voxels": unet.max_voxels,
-                                "model": "3-D U-Net, 3 levels, widths %d/%d/%d, im2col + tcgen05 GEMMs of this "
+                                "model": "3-D U-Net, 3 levels, widths %d/%d/%d, implicit-GEMM tcgen05 convolutions of this "
                                          "project" % (args.ws_unet_width, 2 * args.ws_unet_width,
                                                       4 * args.ws_unet_width)}
     Wx = extrapolate_every_for(nx)
@@ -856,6 +865,88 @@ def main_warmstart(args, ws, rank, local):
                                        f"D3Q19 anodes"},
                 "warm_start": out}
         print(json.dumps(line))
+    return 0
+
+
+def _unet_volumes(n, shape, seed=7):
+    """n synthetic training volumes like the warm-start inputs: 16 feature
+    channels in [0, 1] on fluid voxels (porosity 0.45), the fluid mask, and
+    targets that are a smooth function of them (zero on solid voxels)."""
+    nz, ny, nx = shape
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        m = (rng.random((1, nz, ny, nx)) < 0.45).astype(np.float32)
+        x = np.concatenate([rng.random((16, nz, ny, nx)).astype(np.float32) * m, m], axis=0)
+        t = ((3.0 * x[0:3] - 1.0) * x[3:4] + x[4:7]) * m
+        out.append((x, t.astype(np.float32)))
+    return out
+
+
+def main_unet(args, ws, rank, local):
+    """Training-step time of the 3-D U-Net on this project's kernels
+    (implicit-GEMM tcgen05 convolutions) over --unet-batch synthetic volumes
+    of --unet-shape already on the device; with --unet-torch, the same
+    network and volumes with PyTorch convolutions (TF32, and BF16 autocast)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_1809_01600_gb300 import lbms as L
+    L.load()
+    nx, ny, nz = (int(v) for v in args.unet_shape.split("x"))
+    B, K, W = args.unet_batch, args.unet_steps, max(args.warmup, 3)
+    vols = _unet_volumes(B, (nz, ny, nx))
+    u = L.UNet(width=args.ws_unet_width, max_voxels=B * nx * ny * nz, seed=1)
+    for x, t in vols:
+        u.add_volume(x, t)
+    u.train(W, max_batch=B, lr=args.ws_lr)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0 = u.gemm_calls()
+    e0.record()
+    loss = u.train(K, max_batch=B, lr=args.ws_lr)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    clk = clocks.stop()
+    gemms = (u.gemm_calls() - c0) // K
+    u.close()
+    out = {"metric": "3-D U-Net training step (this project's kernels)", "value": round(ms, 3), "unit": "ms/step",
+           "n_gpus": 1, "steps": K, "warmup": W, "higher_is_better": False, "vs_baseline": None,
+           "dtype": "bf16 (fp32 accumulation, fp32 master weights)", "data": "synthetic",
+           "config": {"workload": f"U-Net width {args.ws_unet_width}, {B} volumes of {args.unet_shape} per step",
+                      "tcgen05_products_per_step": int(gemms), "final_loss": loss},
+           "clocks": clk}
+    if args.unet_torch:
+        dev = torch.device("cuda")
+        xs = torch.tensor(np.stack([x for x, _ in vols]), device=dev)
+        ts = torch.tensor(np.stack([t for _, t in vols]), device=dev)
+        m = xs[:, 16:17]
+        for amp in (False, True):
+            torch.manual_seed(0)
+            model = _unet(torch, args.ws_unet_width).to(dev)
+            opt = torch.optim.Adam(model.parameters(), lr=args.ws_lr)
+
+            def step():
+                with torch.autocast("cuda", dtype=torch.bfloat16, enabled=amp):
+                    pred = model(xs)
+                lo = (((pred.float() - ts) * m) ** 2).sum() / (3.0 * m.sum())
+                opt.zero_grad()
+                lo.backward()
+                opt.step()
+            for _ in range(W):
+                step()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(K):
+                step()
+            e1.record()
+            torch.cuda.synchronize()
+            out["pytorch_bf16_autocast_ms" if amp else "pytorch_tf32_ms"] = round(e0.elapsed_time(e1) / K, 3)
+            del model, opt
+    if rank == 0:
+        print(json.dumps(out))
     return 0
 
 

@@ -141,6 +141,10 @@ lbms_status lbms_unet_create(int width, int64_t max_voxels, uint64_t seed, lbms_
  * data and fit max_voxels. */
 lbms_status lbms_unet_add_sample(lbms_unet *net, lbms_ctx *ctx, int case_index);
 
+/* Adds a caller-given training volume: x FP32 [17][Z][Y][X] (channel 16 the
+ * fluid mask), targets [3][Z][Y][X]; X, Y, Z multiples of 4. */
+lbms_status lbms_unet_add_volume(lbms_unet *net, const float *x, const float *targets, int X, int Y, int Z);
+
 /* iters steps of Adam on the mean-square error over fluid voxels.  Step i
  * takes the training volumes of group i mod G (volumes of equal extents, in
  * order of first addition): min(max_batch, volumes in the group,

@@ -12,14 +12,16 @@
 // store FP32.  Rows and K beyond the operands' extents are zero-filled by
 // TMA, so M and K need no padding; N is a multiple of 64.
 //
-// Two more load modes turn the same kernel into the convolutions of the
-// 3-D U-Net (lbms_unet.cuh), whose activations are stored in a layout with a
-// zero halo of one voxel per side, so that the neighbour of every interior
-// voxel at tap t = (dz, dy, dx) lies a fixed number of rows off(t) away:
-//  * implicit convolution (mode 1): K runs over 27 taps x C channels; the
-//    A tile of tap t is the activation matrix [rows][C] read at rows
-//    m0 + off(t) (TMA zero-fills rows outside it), B the weights [N][27 C];
-//  * weight gradient (mode 2): P[t C + c][n] = sum_r x[r + off(t)][c] dZ[r][n]
+// The convolutions of the 3-D U-Net (lbms_unet.cuh) run on the same
+// machinery.  Its activations are stored in a layout with a zero halo of one
+// voxel per side, so that the neighbour of every interior voxel at tap
+// t = (dz, dy, dx) lies a fixed number of rows off(t) away:
+//  * implicit convolution (umma_conv_kernel below): K runs over 27 taps x C
+//    channels; the A tile of tap t is the activation matrix [rows][C] read
+//    at rows m0 + off(t) (TMA zero-fills rows outside it), one 130-row window
+//    shared by the three taps of a (dz, dy) row; B the weights [N][27 C];
+//  * weight gradient (load mode 2 of umma_gemm_kernel):
+//    P[t C + c][n] = sum_r x[r + off(t)][c] dZ[r][n]
 //    with B = dZ^T [N][rows]; the A tile's two 64-row halves come from three
 //    transposed copies xT_j[c][r] = x[r + j - 1][c] (j = dx + 1) of the
 //    input, each read at inner coordinate r + (dz Yp + dy) Xp, a multiple of
@@ -135,7 +137,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 
 // Load modes of the kernel (see the head of the file).
-constexpr int kModePlain = 0, kModeConv = 1, kModeWgrad = 2;
+constexpr int kModePlain = 0, kModeWgrad = 2;
 
 template <int kMode>
 __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant__ CUtensorMap mapA,
@@ -196,11 +198,7 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
             const int s = kt % kStages;
             uint8_t* sa = base + (size_t)s * kStageBytes;
             mbar_expect_tx(&full[s], kStageBytes);
-            if (kMode == kModeConv) {
-                const int t = kt / taps.per_tap, c = kt - t * taps.per_tap;
-                tma_load_2d(sa, &mapA, c * kUK, m0 + taps.off[t], &full[s]);
-                tma_load_2d(sa + kABytes, &mapB, kt * kUK, n0, &full[s]);
-            } else if (kMode == kModeWgrad) {
+            if (kMode == kModeWgrad) {
                 tma_load_2d(sa, ma2[0], k0 + kt * kUK + shift2[0], c2[0], &full[s]);
                 tma_load_2d(sa + kABytes / 2, ma2[1], k0 + kt * kUK + shift2[1], c2[1], &full[s]);
                 tma_load_2d(sa + kABytes, &mapB, k0 + kt * kUK, n0, &full[s]);
@@ -273,6 +271,142 @@ __global__ void __launch_bounds__(128, 1) umma_gemm_kernel(const __grid_constant
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Implicit 3x3x3 convolution with the A tile shared by the three taps of a
+// (dz, dy) row.  Those taps differ in dx only, so their A tiles are the same
+// activation rows shifted by one: one TMA box of 130 rows (the window from
+// the tap with the lowest offset) serves all three, each MMA reading it
+// from row 0, 1 or 2.  The 128-byte swizzle is a function of the shared
+// address bits, as TMA wrote it, so a descriptor whose start is s rows
+// (128 s bytes) into the window reads those rows correctly with matrix base
+// offset 0 (checked against a CPU implicit-GEMM reference; base offset
+// (start >> 7) & 7 gives wrong products).  A stage holds the window and the
+// three taps' 64 x 64 B tiles; K runs over 9 rows of taps x C / 64 channel
+// blocks.
+constexpr int kCRows = kUM + 2;                                   // window rows
+constexpr int kCABytes = (kCRows * kUK * 2 + 1023) / 1024 * 1024;  // 17 KiB (1024-aligned B tiles follow)
+constexpr int kCStageBytes = kCABytes + 3 * kBBytes;
+constexpr int kCStages = 2;                                       // two CTAs fit on an SM
+constexpr size_t kCSmemBytes = 1024 + (size_t)kCStages * kCStageBytes + 256;
+
+__global__ void __launch_bounds__(128, 1) umma_conv_kernel(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB,
+                                                           float* __restrict__ P, int M, int N, int cpt,
+                                                           unsigned int* __restrict__ err,
+                                                           const __grid_constant__ ConvTaps taps) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kCStages * kCStageBytes);
+    uint64_t* empty = full + kCStages;
+    uint64_t* done = empty + kCStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * kUN, m0 = blockIdx.y * kUM;
+    const int nk = 9 * cpt;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kCStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;
+        // the lowest of the three offsets of tap row g: the window's first row
+        auto low = [&](int g) {
+            const int a = taps.off[3 * g], b = taps.off[3 * g + 1], c = taps.off[3 * g + 2];
+            return min(a, min(b, c));
+        };
+        auto load = [&](int kt) {
+            const int s = kt % kCStages;
+            const int g = kt / cpt, c = kt - g * cpt;
+            uint8_t* sa = base + (size_t)s * kCStageBytes;
+            mbar_expect_tx(&full[s], kCRows * kUK * 2 + 3 * kBBytes);
+            tma_load_2d(sa, &mapA, c * kUK, m0 + low(g), &full[s]);
+            for (int d = 0; d < 3; ++d)
+                tma_load_2d(sa + kCABytes + d * kBBytes, &mapB, ((3 * g + d) * cpt + c) * kUK, n0, &full[s]);
+            ++issued;
+        };
+        for (int kt = 0; kt < nk && kt < kCStages; ++kt) load(kt);
+        int consumed = 0;
+        for (int kt = 0; kt < nk; ++kt) {
+            const int s = kt % kCStages;
+            const uint32_t ph = (uint32_t)(kt / kCStages) & 1u;
+            if (!mbar_wait(&full[s], ph)) {
+                ok = false;
+                break;
+            }
+            ++consumed;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int g = kt / cpt;
+            const int lo = low(g);
+            const uint32_t a = smem_u32(base + (size_t)s * kCStageBytes);
+            for (int d = 0; d < 3; ++d) {
+                const uint32_t arow = a + 128u * (uint32_t)(taps.off[3 * g + d] - lo);
+                const uint32_t b = a + kCABytes + d * kBBytes;
+#pragma unroll
+                for (int j = 0; j < kUK / 16; ++j)
+                    umma_f16(tmem, sw128_desc(arow + 32 * j), sw128_desc(b + 32 * j), (kt | d | j) != 0 ? 1u : 0u);
+            }
+            umma_commit(&empty[s]);
+            if (kt + kCStages < nk) {
+                if (!mbar_wait(&empty[s], ph)) {
+                    ok = false;
+                    break;
+                }
+                load(kt + kCStages);
+            }
+        }
+        umma_commit(done);
+        if (!ok) {
+            atomicOr(err, 1u);
+            for (int kt = consumed; kt < issued; ++kt) mbar_wait(&full[kt % kCStages], (uint32_t)(kt / kCStages) & 1u);
+        }
+    }
+    __syncwarp();
+    const bool got = mbar_wait(done, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (!got) {
+        if (lane == 0) atomicOr(err, 2u);
+    } else {
+        const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+        uint32_t v0[32], v1[32];
+        tmem_ld32(taddr, v0);
+        tmem_ld32(taddr + 32, v1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = m0 + 32 * warp + lane;
+        if (row < M) {
+            float4* dst = reinterpret_cast<float4*>(P + (int64_t)row * N + n0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dst[q] = make_float4(__uint_as_float(v0[4 * q]), __uint_as_float(v0[4 * q + 1]),
+                                     __uint_as_float(v0[4 * q + 2]), __uint_as_float(v0[4 * q + 3]));
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                dst[8 + q] = make_float4(__uint_as_float(v1[4 * q]), __uint_as_float(v1[4 * q + 1]),
+                                         __uint_as_float(v1[4 * q + 2]), __uint_as_float(v1[4 * q + 3]));
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_once;
 cudaError_t g_init = cudaErrorNotReady;
@@ -289,11 +423,10 @@ void init_once() {
     g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModePlain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)kSmemBytes);
     if (g_init == cudaSuccess)
-        g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModeConv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kSmemBytes);
-    if (g_init == cudaSuccess)
         g_init = cudaFuncSetAttribute(umma_gemm_kernel<kModeWgrad>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kSmemBytes);
+    if (g_init == cudaSuccess)
+        g_init = cudaFuncSetAttribute(umma_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCSmemBytes);
 }
 
 // 2-D tensor map of a K-contiguous BF16 operand: inner extent K, `rows`
@@ -342,10 +475,16 @@ cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N,
     if (rows < 1 || C < kUK || C % kUK || N < kUN || N % kUN || taps.per_tap != C / kUK ||
         (rows + kUM - 1) / kUM > 65535 || ((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(W)) & 15u))
         return cudaErrorInvalidValue;
+    for (int g = 0; g < 9; ++g) {   // the three taps of a row lie in one window: offsets o, o + 1, o + 2
+        const int a = taps.off[3 * g], b = taps.off[3 * g + 1], c = taps.off[3 * g + 2];
+        const int lo = a < b ? (a < c ? a : c) : (b < c ? b : c);
+        if (a - lo > 2 || b - lo > 2 || c - lo > 2 || a == b || b == c || a == c) return cudaErrorInvalidValue;
+    }
     CUtensorMap ma, mb;
-    if (!make_map(&ma, x, C, rows, C, kUM) || !make_map(&mb, W, 27 * C, N, 27 * C, kUN)) return cudaErrorInvalidValue;
+    if (!make_map(&ma, x, C, rows, C, kCRows) || !make_map(&mb, W, 27 * C, N, 27 * C, kUN))
+        return cudaErrorInvalidValue;
     const dim3 grid(N / kUN, (rows + kUM - 1) / kUM, 1);
-    umma_gemm_kernel<kModeConv><<<grid, 128, kSmemBytes, st>>>(ma, mb, mb, mb, P, rows, N, 27 * C, err, taps);
+    umma_conv_kernel<<<grid, 128, kCSmemBytes, st>>>(ma, mb, P, rows, N, C / kUK, err, taps);
     return cudaGetLastError();
 }
 

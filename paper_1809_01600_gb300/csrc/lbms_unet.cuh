@@ -1018,6 +1018,46 @@ lbms_status lbms_unet_add_sample(lbms_unet* u, lbms_ctx* ctx, int k) {
     return LBMS_OK;
 }
 
+lbms_status lbms_unet_add_volume(lbms_unet* u, const float* x, const float* t, int X, int Y, int Z) {
+    if (!u || !x || !t) return LBMS_EINVAL;
+    if (X < 4 || Y < 4 || Z < 4 || X % 4 || Y % 4 || Z % 4)
+        return ufail(u, LBMS_EINVAL, "volume extents must be multiples of 4");
+    const Geo g = make_geo(1, X, Y, Z);
+    if (g.V > u->vcap || !levels_fit(levels_of(1, X, Y, Z)))
+        return ufail(u, LBMS_EINVAL, "the volume holds %lld voxels, the network was made for %lld", (long long)g.V,
+                     (long long)u->vcap);
+    double nf = 0.0;
+    for (int64_t s = 0; s < g.V; ++s) nf += x[(int64_t)(kUInReal - 1) * g.V + s];
+    lbms_unet::Sample s;
+    s.X = X;
+    s.Y = Y;
+    s.Z = Z;
+    s.rows = g.R;
+    s.nfluid = (int64_t)std::llround(nf);
+    float* dev = nullptr;
+    const size_t nin = (size_t)g.V * kUInReal, ntg = (size_t)g.V * 3;
+    if (cudaMalloc(&dev, (nin + ntg) * sizeof(float)) != cudaSuccess) return ufail(u, LBMS_ENOMEM, "volume upload");
+    cudaError_t e = cudaMalloc(&s.in, (size_t)g.R * kUInC * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMalloc(&s.tg, (size_t)g.R * 4 * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(dev, x, nin * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dev + nin, t, ntg * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(s.in, 0, (size_t)g.R * kUInC * sizeof(bf16));
+    if (e == cudaSuccess) e = cudaMemset(s.tg, 0, (size_t)g.R * 4 * sizeof(float));
+    if (e == cudaSuccess) {
+        vol_in_kernel<<<warp_grid(g.V), 256>>>(dev, g, s.in, s.tg);
+        vol_target_kernel<<<grid_for(g.V), 256>>>(dev + nin, g, s.tg);
+        e = cudaDeviceSynchronize();
+    }
+    cudaFree(dev);
+    if (e != cudaSuccess) {
+        cudaFree(s.in);
+        cudaFree(s.tg);
+        return ufail(u, LBMS_ECUDA, "volume upload: %s", cudaGetErrorString(e));
+    }
+    u->samples.push_back(s);
+    return LBMS_OK;
+}
+
 lbms_status lbms_unet_train(lbms_unet* u, int iters, int max_batch, double lr, double* last_loss) {
     if (!u) return LBMS_EINVAL;
     if (iters < 0 || max_batch < 1 || !(lr > 0.0))

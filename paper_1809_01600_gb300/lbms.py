@@ -41,7 +41,8 @@ NET_EXPORTS = ("lbms_net_create", "lbms_net_add_sample", "lbms_net_features", "l
                "lbms_net_warm_start", "lbms_net_set_gemm", "lbms_net_gemm_calls",
                "lbms_net_forward", "lbms_net_train_batch", "lbms_net_get", "lbms_net_set", "lbms_net_info",
                "lbms_net_last_error", "lbms_net_destroy")
-UNET_EXPORTS = ("lbms_unet_create", "lbms_unet_add_sample", "lbms_unet_train", "lbms_unet_warm_start",
+UNET_EXPORTS = ("lbms_unet_create", "lbms_unet_add_sample", "lbms_unet_add_volume", "lbms_unet_train",
+                "lbms_unet_warm_start",
                 "lbms_unet_forward", "lbms_unet_train_batch", "lbms_unet_get", "lbms_unet_set", "lbms_unet_info",
                 "lbms_unet_gemm_calls", "lbms_unet_last_error", "lbms_unet_destroy")
 
@@ -152,6 +153,7 @@ def load(build_if_needed: bool = True):
         "lbms_net_destroy": (None, [P]),
         "lbms_unet_create": (st, [C.c_int, I64, C.c_uint64, C.POINTER(P)]),
         "lbms_unet_add_sample": (st, [P, P, C.c_int]),
+        "lbms_unet_add_volume": (st, [P, P, P, C.c_int, C.c_int, C.c_int]),
         "lbms_unet_train": (st, [P, C.c_int, C.c_int, C.c_double, D]),
         "lbms_unet_warm_start": (st, [P, P, C.c_int, D]),
         "lbms_unet_forward": (st, [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P]),
@@ -623,6 +625,13 @@ class UNet:
 
     def add_sample(self, handle, case=0):
         self._check(self._lib.lbms_unet_add_sample(self._h, handle._h, int(case)))
+
+    def add_volume(self, x, targets):
+        """A training volume x float32 [17, Z, Y, X] with targets [3, Z, Y, X]."""
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        _, Z, Y, X = x.shape
+        self._check(self._lib.lbms_unet_add_volume(self._h, x.ctypes.data, t.ctypes.data, X, Y, Z))
 
     def train(self, iters, max_batch=8, lr=1e-3):
         loss = C.c_double()
