@@ -347,7 +347,7 @@ def time_steps(L, case, precision, args, dist):
                          "traffic": ncu_traffic(case.name, precision, variant_key(info))}}
 
 
-def _run_form(L, case, label, prec, W, init, tol, args, net=None, X0=None, modes=1):
+def _run_form(L, case, label, prec, W, init, tol, args, net=None, X0=None, modes=1, unet=None):
     """One time-to-residual run on a fresh handle, timed from its boundary
     data being set (the network's prediction, when it starts from one, is
     inside the time) to the residual check that meets tol; clocks sampled
@@ -362,6 +362,8 @@ def _run_form(L, case, label, prec, W, init, tol, args, net=None, X0=None, modes
     t = time.perf_counter()
     if init == "network":
         net.warm_start(s)
+    elif init == "unet":
+        unet.warm_start(s)
     elif X0 is not None:
         s.set_fields(X0)
     n, r, st = s.run_to_residual(tol, args.max_steps, raise_on_fail=False)
@@ -391,6 +393,7 @@ def time_to_residual(L, case, args):
              "fp32_extrapolated": ("fp32", Wx, "uniform", 1),
              "fp16_extrapolated_profile1d": ("fp16", Wx, "profile1d", 1),
              "fp16_extrapolated_network": ("fp16", Wx, "network", 1),
+             "fp16_extrapolated_unet": ("fp16", Wx, "unet", 1),
              "fp32_rre": ("fp32", Wr, "uniform", M),
              "fp16_rre": ("fp16", Wr, "uniform", M),
              "fp16_rre_network": ("fp16", Wr, "network", M)}
@@ -400,22 +403,36 @@ def time_to_residual(L, case, args):
             raise SystemExit(f"unknown time-to-residual form {f}")
     chosen = args.ttr_chosen if args.ttr_chosen in pick else pick[-1]
     out = {"tol": tol, "chosen": chosen, "baseline": "plain_fp32"}
-    net = None
-    if any(forms[f][2] == "network" for f in pick):
+    net = unet = None
+    if any(forms[f][2] in ("network", "unet") for f in pick):
+        import torch
         from workloads import cases as W_
-        net, info = train_warmstart_net(L, W_.warmstart_cases(args.ws_train, 1000), 1e-8, args)
+        if any(forms[f][2] == "unet" for f in pick):
+            vox = int(np.prod([(d + 3) // 4 * 4 for d in case.solid.shape]))
+            unet = L.UNet(width=args.ws_unet_width, max_voxels=max(8 * 64 * 32 * 32, vox), seed=1)
+        net, info = train_warmstart_net(L, W_.warmstart_cases(args.ws_train, 1000), 1e-8, args, unet=unet)
         out["network"] = dict(info, note="trained on 64x32x32 anodes, none of them this one; the "
                                          "training is outside the form's seconds, the prediction inside")
+        if unet is not None:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            uloss = unet.train(args.ws_unet_iters, max_batch=8, lr=args.ws_lr)
+            torch.cuda.synchronize()
+            out["unet"] = {"params": unet.info()[0], "iters": args.ws_unet_iters, "final_loss": uloss,
+                           "seconds": round(time.perf_counter() - t0, 2),
+                           "note": "the same 64x32x32 steady states; training outside the form's seconds"}
     start = None      # end state of the chosen form: where the reference starts
     for label in pick:
         prec, W, init, modes = forms[label]
-        s, res = _run_form(L, case, label, prec, W, init, tol, args, net=net, modes=modes)
+        s, res = _run_form(L, case, label, prec, W, init, tol, args, net=net, modes=modes, unet=unet)
         out[label] = res
         if label == chosen:
             start = s.fields()
         s.close()
     if net is not None:
         net.close()
+    if unet is not None:
+        unet.close()
     base = out.get("plain_fp32")
     for label in pick:
         if base and label != "plain_fp32":
