@@ -108,6 +108,8 @@ def parse():
     ap.add_argument("--ws-unet-iters", type=int, default=6000,
                     help="warm start: Adam steps of the 3-D U-Net on this project's kernels (0 skips it)")
     ap.add_argument("--ws-unet-width", type=int, default=28, help="warm start: U-Net width (28: 1.05M parameters)")
+    ap.add_argument("--ws-starts", default="uniform,profile1d,network,unet",
+                    help="warm start: the starts timed on the held-out anodes")
     ap.add_argument("--unet-shape", default="96x96x96", help="--workload unet: volume grid (nx x ny x nz)")
     ap.add_argument("--unet-batch", type=int, default=8, help="--workload unet: volumes per training step")
     ap.add_argument("--unet-steps", type=int, default=20, help="--workload unet: timed training steps")
@@ -832,7 +834,7 @@ def main_warmstart(args, ws, rank, local):
         forms.insert(0, ("plain_fp32", "fp32", 0, 1))
     for label, prec, Wx, modes in forms:
         res = {"extrapolate_every": Wx, "extrapolate_modes": modes}
-        starts = ("uniform", "profile1d", "network") + (("unet",) if unet is not None else ())
+        starts = [st for st in args.ws_starts.split(",") if st and (st != "unet" or unet is not None)]
         for start in starts:
             bt = L.Batch.from_cases(test, precision=prec, extrapolate_every=Wx, extrapolate_modes=modes,
                                     init_mode="profile1d" if start == "profile1d" else "uniform")
@@ -860,7 +862,7 @@ def main_warmstart(args, ws, rank, local):
         if args.ws_compare_unet and label == "fp16_extrapolated":
             res["unet_pytorch"] = compare_unet(L, net, kept, test, tol, prec, Wx, modes, args)
         for start in ("profile1d", "network", "unet", "unet_pytorch"):
-            if start in res:
+            if start in res and "uniform" in res:
                 res[start]["steps_vs_uniform"] = round(res[start]["mean_steps"] / res["uniform"]["mean_steps"], 3)
         out[label] = res
     tc, ms = net.gemm_calls()
@@ -870,10 +872,11 @@ def main_warmstart(args, ws, rank, local):
         out["unet_gemm_calls"] = {"tcgen05": unet.gemm_calls()}
         unet.close()
     if rank == 0:
-        chosen = "unet" if unet is not None else "network"
-        v = out["fp16_extrapolated"][chosen]["mean_steps"]
+        res0 = out["fp16_extrapolated"]
+        chosen = next(c for c in ("unet", "network", "profile1d", "uniform") if c in res0)
+        v = res0[chosen]["mean_steps"]
         line = {"metric": "steps to residual (held-out anodes, %s start, FP16 + extrapolation)"
-                          % ("U-Net" if chosen == "unet" else "network"), "value": v,
+                          % {"unet": "U-Net", "network": "network"}.get(chosen, chosen), "value": v,
                 "unit": "steps", "n_gpus": 1, "higher_is_better": False, "vs_baseline": None,
                 "dtype": "bf16 network, f32 LBM", "data": "synthetic",
                 "config": {"workload": f"learned warm start, {len(train)} training anodes "

@@ -144,8 +144,18 @@ struct ConvTaps {
     int per_tap = 1;
     int off[27] = {};
 };
+// Optional epilogue of umma_conv_gemm: instead of FP32 P, out[r][n] =
+// BF16(relu(P[r][n] + bias[n])) on the interior rows of the zero-halo layout
+// (volumes of X x Y x Z voxels in Xp x Yp x Zp rows, R rows in all) and 0 on
+// every other row.
+struct ConvEpilogue {
+    const float* bias = nullptr;
+    void* out = nullptr;          // BF16 [rows][N]
+    int X = 0, Y = 0, Z = 0, Xp = 0, Yp = 0, Zp = 0;
+    long long R = 0;
+};
 cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N, const ConvTaps& taps, float* P,
-                           unsigned int* err, cudaStream_t st);
+                           unsigned int* err, cudaStream_t st, const ConvEpilogue* ep = nullptr);
 cudaError_t umma_wgrad_gemm(const void* dzT, int N, const void* const xT[3], int C, int rows, int S,
                             const ConvTaps& taps, float* P, unsigned int* err, cudaStream_t st);
 

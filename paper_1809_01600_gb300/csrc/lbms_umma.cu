@@ -293,7 +293,8 @@ __global__ void __launch_bounds__(128, 1) umma_conv_kernel(const __grid_constant
                                                            const __grid_constant__ CUtensorMap mapB,
                                                            float* __restrict__ P, int M, int N, int cpt,
                                                            unsigned int* __restrict__ err,
-                                                           const __grid_constant__ ConvTaps taps) {
+                                                           const __grid_constant__ ConvTaps taps,
+                                                           const __grid_constant__ ConvEpilogue ep) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     uint64_t* full = reinterpret_cast<uint64_t*>(base + (size_t)kCStages * kCStageBytes);
@@ -389,7 +390,36 @@ __global__ void __launch_bounds__(128, 1) umma_conv_kernel(const __grid_constant
         tmem_ld32(taddr + 32, v1);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int row = m0 + 32 * warp + lane;
-        if (row < M) {
+        if (row < M && ep.out) {
+            // bias + ReLU + BF16 on interior rows of the zero-halo layout, 0 elsewhere
+            bool in = row < ep.R;
+            if (in) {
+                unsigned q = (unsigned)row;
+                const int x = (int)(q % (unsigned)ep.Xp) - 1;
+                q /= (unsigned)ep.Xp;
+                const int y = (int)(q % (unsigned)ep.Yp) - 1;
+                q /= (unsigned)ep.Yp;
+                const int z = (int)(q % (unsigned)ep.Zp) - 1;
+                in = x >= 0 && x < ep.X && y >= 0 && y < ep.Y && z >= 0 && z < ep.Z;
+            }
+            const float* bias = ep.bias + n0;
+            uint4* dst = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(ep.out) + (int64_t)row * N + n0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                uint32_t w[4];
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int c = 8 * q + 2 * h;
+                    const uint32_t* v = c < 32 ? v0 : v1;
+                    const int cc = c & 31;
+                    const float a = in ? fmaxf(__uint_as_float(v[cc]) + bias[c], 0.0f) : 0.0f;
+                    const float b = in ? fmaxf(__uint_as_float(v[cc + 1]) + bias[c + 1], 0.0f) : 0.0f;
+                    const __nv_bfloat162 pr = __floats2bfloat162_rn(a, b);
+                    w[h] = *reinterpret_cast<const uint32_t*>(&pr);
+                }
+                dst[q] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        } else if (row < M) {
             float4* dst = reinterpret_cast<float4*>(P + (int64_t)row * N + n0);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
@@ -469,7 +499,7 @@ cudaError_t umma_gemm_tn(const void* A, int lda, const void* B, int ldb, float* 
 }
 
 cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N, const ConvTaps& taps, float* P,
-                           unsigned int* err, cudaStream_t st) {
+                           unsigned int* err, cudaStream_t st, const ConvEpilogue* ep) {
     cudaError_t e = umma_gemm_init();
     if (e != cudaSuccess) return e;
     if (rows < 1 || C < kUK || C % kUK || N < kUN || N % kUN || taps.per_tap != C / kUK ||
@@ -484,7 +514,11 @@ cudaError_t umma_conv_gemm(const void* x, int rows, int C, const void* W, int N,
     if (!make_map(&ma, x, C, rows, C, kCRows) || !make_map(&mb, W, 27 * C, N, 27 * C, kUN))
         return cudaErrorInvalidValue;
     const dim3 grid(N / kUN, (rows + kUM - 1) / kUM, 1);
-    umma_conv_kernel<<<grid, 128, kCSmemBytes, st>>>(ma, mb, P, rows, N, C / kUK, err, taps);
+    if (ep && (!ep->bias || !ep->out || (reinterpret_cast<uintptr_t>(ep->out) & 15u) || ep->Xp < 1 || ep->Yp < 1 ||
+               ep->Zp < 1))
+        return cudaErrorInvalidValue;
+    umma_conv_kernel<<<grid, 128, kCSmemBytes, st>>>(ma, mb, P, rows, N, C / kUK, err, taps,
+                                                     ep ? *ep : ConvEpilogue{});
     return cudaGetLastError();
 }
 

@@ -59,20 +59,6 @@ __device__ __forceinline__ int64_t voxel_row(const Geo& g, int b, int x, int y, 
 __device__ __forceinline__ int64_t warp_id() { return ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
 __device__ __forceinline__ int64_t warp_count() { return ((int64_t)gridDim.x * blockDim.x) >> 5; }
 
-// Convolution epilogue: out[r][c] = relu(P[r][c] + b[c]) on interior rows, 0 elsewhere.
-__global__ void bias_relu_rows_kernel(const float* __restrict__ P, const float* __restrict__ bias, Geo g, int C,
-                                      bf16* __restrict__ out) {
-    const int lane = threadIdx.x & 31;
-    for (int64_t r = warp_id(); r < g.Rp; r += warp_count()) {
-        int x, y, z, b;
-        const bool in = row_voxel(g, r, x, y, z, b);
-        for (int c = lane; c < C; c += 32) {
-            const float v = in ? P[r * C + c] + bias[c] : 0.0f;
-            out[r * C + c] = __float2bfloat16_rn(v > 0.0f ? v : 0.0f);
-        }
-    }
-}
-
 // dst[r][c] = P[r][c] on interior rows, 0 elsewhere (FP32 gradients).
 __global__ void mask_rows_kernel(const float* __restrict__ P, Geo g, int C, float* __restrict__ dst) {
     const int lane = threadIdx.x & 31;
@@ -639,21 +625,27 @@ lbms_status mask_rows(lbms_unet* u, const Geo& g, int C, float* dst) {
 }
 
 // ------------------------------------------------------ layer passes
-// relu(conv3(x) + b) -> out (kind 3: implicit GEMM), or the 1x1 head's product (left in P)
+// relu(conv3(x) + b) -> out (kind 3: implicit GEMM), or the 1x1 head's product (left in P, out unused)
 lbms_status conv_fwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const Geo& g, bf16* out) {
     if (l.kind == 3) {
-        if ((size_t)g.Rp * l.co_s > u->P_floats) return ufail(u, LBMS_EINVAL, "U-Net convolution too large");
+        // bias, ReLU, the zero halo and the BF16 store happen in the GEMM's epilogue
         const lbms::ConvTaps tp = conv_taps(g, l.ci_s / 64, 1);
-        UCK(lbms::umma_conv_gemm(x, (int)g.Rp, l.ci_s, l.Wb, l.co_s, tp, u->P, u->gemm_err, 0), "convolution");
+        lbms::ConvEpilogue ep;
+        ep.bias = l.b;
+        ep.out = out;
+        ep.X = g.X;
+        ep.Y = g.Y;
+        ep.Z = g.Z;
+        ep.Xp = g.Xp;
+        ep.Yp = g.Yp;
+        ep.Zp = g.Zp;
+        ep.R = g.R;
+        if (!out) return ufail(u, LBMS_EINVAL, "U-Net convolution without an output");
+        UCK(lbms::umma_conv_gemm(x, (int)g.Rp, l.ci_s, l.Wb, l.co_s, tp, u->P, u->gemm_err, 0, &ep), "convolution");
         ++u->tcgen05_calls;
-    } else {
-        UST(ugemm(u, x, l.ci_s, l.Wb, l.K, g.Rp, l.rows, l.K, 1));
+        return LBMS_OK;
     }
-    if (out) {
-        bias_relu_rows_kernel<<<warp_grid(g.Rp), 256>>>(u->P, l.b, g, l.co_s, out);
-        UCK(cudaGetLastError(), "bias relu");
-    }
-    return LBMS_OK;
+    return ugemm(u, x, l.ci_s, l.Wb, l.K, g.Rp, l.rows, l.K, 1);   // the 1x1 head: P [Rp][64]
 }
 
 // transposed 2x2x2 convolution of x [lo.Rp][ci_s] -> y [hi.Rp][co_s]
@@ -665,8 +657,11 @@ lbms_status up_fwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const
 }
 
 // Backward pass of a 3x3x3 convolution + ReLU from dA (the gradient of its
-// output a): weight and bias gradients and, with dx, the input gradient
-// [Rp][ci_s] (zero outside the volumes).
+// output a; it may be u->P): weight and bias gradients and, with dx, the
+// input gradient [Rp][ci_s]: masked to zero outside the volumes into dx, or
+// left unmasked in u->P when dx is u->P (for a ReLU backward or a pooling
+// gradient next, which read only what the zero halo of their activations
+// lets through).
 lbms_status conv_bwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const bf16* a, const float* dA,
                      const Geo& g, float* dx) {
     relu_back_rows_kernel<<<(unsigned)(g.Rp / 64), 256>>>(dA, a, g.Rp, l.co_s, u->dz, l.gb);
@@ -687,7 +682,7 @@ lbms_status conv_bwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, con
     const lbms::ConvTaps tn = conv_taps(g, l.co_s / 64, -1);
     UCK(lbms::umma_conv_gemm(u->dz, (int)g.Rp, l.co_s, l.Wt, l.ci_s, tn, u->P, u->gemm_err, 0), "input gradient");
     ++u->tcgen05_calls;
-    return mask_rows(u, g, l.ci_s, dx);
+    return dx == u->P ? LBMS_OK : mask_rows(u, g, l.ci_s, dx);
 }
 
 // Backward pass of the transposed convolution from dy [hi.Rp][co_s]: weight
@@ -705,7 +700,7 @@ lbms_status up_bwd(lbms_unet* u, const lbms_unet::Layer& l, const bf16* x, const
     splitk_sum_kernel<<<grid_for((int64_t)l.rows * l.K), 256>>>(u->P, lo.S, (int64_t)l.rows * l.K, l.g);
     UCK(cudaGetLastError(), "split-k sum");
     UST(ugemm(u, u->G, l.rows, l.Wt, l.rows, lo.Rp, l.ci_s, l.rows, 1));
-    return mask_rows(u, lo, l.ci_s, dx);
+    return dx == u->P ? LBMS_OK : mask_rows(u, lo, l.ci_s, dx);
 }
 
 // ------------------------------------------------------ network passes
@@ -756,32 +751,35 @@ lbms_status unet_backward(lbms_unet* u, const Levels& v, float inv_n) {
     splitk_sum_kernel<<<grid_for((int64_t)h.rows * h.K), 256>>>(u->P, g0.S, (int64_t)h.rows * h.K, h.g);
     UCK(cudaGetLastError(), "split-k sum");
     UST(ugemm(u, u->dz, kUOutC, h.Wt, h.rows, g0.Rp, h.ci_s, h.rows, 1));
-    UST(mask_rows(u, g0, h.ci_s, u->fa));
+    // Input gradients stay in P (unmasked) when a ReLU backward or a pooling
+    // gradient reads them next; the two that feed a concatenation's split
+    // are masked into fa / fb (the split's halves reach bias column sums).
+    float* P = u->P;
     // decoder, level 0
-    UST(conv_bwd(u, L[11], u->d1a, u->d1, u->fa, g0, u->fb));
-    UST(conv_bwd(u, L[10], u->c1, u->d1a, u->fb, g0, u->fa));
+    UST(conv_bwd(u, L[11], u->d1a, u->d1, P, g0, P));
+    UST(conv_bwd(u, L[10], u->c1, u->d1a, P, g0, u->fa));
     split_kernel<<<grid_for(g0.Rp * 64), 256>>>(u->fa, 64, w, w, 64, 64, g0.Rp, u->fb, u->fc);
     UCK(cudaGetLastError(), "split");
-    UST(up_bwd(u, L[9], u->d2, u->fb, g1, g0, u->fd));
+    UST(up_bwd(u, L[9], u->d2, u->fb, g1, g0, P));
     // decoder, level 1
-    UST(conv_bwd(u, L[8], u->d2a, u->d2, u->fd, g1, u->fa));
-    UST(conv_bwd(u, L[7], u->c2, u->d2a, u->fa, g1, u->fb));
+    UST(conv_bwd(u, L[8], u->d2a, u->d2, P, g1, P));
+    UST(conv_bwd(u, L[7], u->c2, u->d2a, P, g1, u->fb));
     split_kernel<<<grid_for(g1.Rp * 64), 256>>>(u->fb, 128, 2 * w, 2 * w, 64, 64, g1.Rp, u->fa, u->fd);
     UCK(cudaGetLastError(), "split");
-    UST(up_bwd(u, L[6], u->e3, u->fa, g2, g1, u->fb));
+    UST(up_bwd(u, L[6], u->e3, u->fa, g2, g1, P));
     // bottom, level 2
-    UST(conv_bwd(u, L[5], u->e3a, u->e3, u->fb, g2, u->fa));
-    UST(conv_bwd(u, L[4], u->p2, u->e3a, u->fa, g2, u->fb));
-    pool_back_rows_kernel<<<warp_grid(g1.R), 256>>>(u->fb, u->arg2, g1, g2, 64, u->fd);
+    UST(conv_bwd(u, L[5], u->e3a, u->e3, P, g2, P));
+    UST(conv_bwd(u, L[4], u->p2, u->e3a, P, g2, P));
+    pool_back_rows_kernel<<<warp_grid(g1.R), 256>>>(P, u->arg2, g1, g2, 64, u->fd);
     UCK(cudaGetLastError(), "pool backward");
     // encoder, level 1
-    UST(conv_bwd(u, L[3], u->e2a, u->e2, u->fd, g1, u->fa));
-    UST(conv_bwd(u, L[2], u->p1, u->e2a, u->fa, g1, u->fb));
-    pool_back_rows_kernel<<<warp_grid(g0.R), 256>>>(u->fb, u->arg1, g0, g1, 64, u->fc);
+    UST(conv_bwd(u, L[3], u->e2a, u->e2, u->fd, g1, P));
+    UST(conv_bwd(u, L[2], u->p1, u->e2a, P, g1, P));
+    pool_back_rows_kernel<<<warp_grid(g0.R), 256>>>(P, u->arg1, g0, g1, 64, u->fc);
     UCK(cudaGetLastError(), "pool backward");
     // encoder, level 0
-    UST(conv_bwd(u, L[1], u->e1a, u->e1, u->fc, g0, u->fa));
-    return conv_bwd(u, L[0], u->x0, u->e1a, u->fa, g0, nullptr);
+    UST(conv_bwd(u, L[1], u->e1a, u->e1, u->fc, g0, P));
+    return conv_bwd(u, L[0], u->x0, u->e1a, P, g0, nullptr);
 }
 
 // The BF16 copies of one layer's weights from its FP32 master copy.
