@@ -9,7 +9,13 @@
  * other start, and its result is the one that counts.  The paper has no network:
  * this is an addition on top of its method.
  *
- * Model: a pointwise multilayer perceptron.  Every fluid cell gets a feature
+ * Two models.  lbms_unet_* (at the end of this file) is a 3-D U-Net whose
+ * convolutions are implicit GEMMs on the tcgen05 tensor cores; it sees the
+ * pore structure and is the better start at the grid it was trained on.
+ * lbms_net_* is a pointwise multilayer perceptron, described here, which
+ * carries over to longer anodes than it was trained on.
+ *
+ * Pointwise model.  Every fluid cell gets a feature
  * row built on the GPU from the solid mask and the boundary data: the
  * Section 4.1 profile at its x, x / L, the fluid fraction of cubes of
  * half-width 1, 3 and 7 cells around it, the cross-section porosity at x and
@@ -21,8 +27,8 @@
  * Adam.
  *
  * All functions return an lbms_status and never abort; buffers are host
- * memory owned by the caller unless stated otherwise.  A net is not thread
- * safe; its device work runs on the legacy default stream. */
+ * memory owned by the caller unless stated otherwise.  A net (either model)
+ * is not thread safe; its device work runs on the legacy default stream. */
 #ifndef LBMS_NET_H
 #define LBMS_NET_H
 

@@ -1,8 +1,7 @@
 // The convolutional warm start (declared in include/lbms_net.h): a 3-D U-Net
 // over the anode's voxels, trained and run with this file's kernels and the
-// tcgen05 GEMM of lbms_umma.cu.  Included at the end of lbms_net.cu, whose
-// feature builder, ReLU-backward, split-K sum, Adam and weight-cast kernels
-// it shares.
+// tcgen05 kernels of lbms_umma.cu.  Included at the end of lbms_net.cu, whose
+// feature builder, split-K sum, Adam and weight-cast kernels it shares.
 //
 // Layout.  Activations are channels-last BF16 rows [row][C] (C a multiple
 // of 64, the real channels first, zeros after).  Each volume of X x Y x Z
@@ -12,13 +11,16 @@
 // (S chunks of the reductions over rows).  The neighbour of a voxel at tap
 // (dz, dy, dx) is then off = (dz Yp + dy) Xp + dx rows away, so a 3x3x3
 // convolution is an implicit GEMM on the tensor cores: the A tile of each
-// tap is the activation matrix read at a shifted row (lbms_umma.cu, mode 1);
-// its input gradient is the same with the flipped weights and negated
-// offsets, its weight gradient a product over rows against three shifted
-// transposed copies of the input (mode 2).  Every kernel that writes an
-// activation or a gradient writes all its rows, zeros outside the volumes,
-// so the halo reads as zero padding whatever batch used the buffers before.
-// The 2x2x2 transposed convolution of the decoder is one product whose 8 C
+// tap is the activation matrix read at a shifted row (umma_conv_kernel,
+// whose epilogue also adds the bias, applies ReLU and the zero halo and
+// stores BF16).  Its input gradient is the same with the flipped weights
+// and negated offsets, its weight gradient a product over rows against
+// three shifted transposed copies of the input (load mode 2 of
+// umma_gemm_kernel).  Every kernel that writes an activation writes all its
+// rows, zeros outside the volumes, so the halo reads as zero padding
+// whatever batch used the buffers before; an input gradient is masked the
+// same way where its reader needs it (unet_backward says which).  The
+// 2x2x2 transposed convolution of the decoder is one product whose 8 C
 // columns go to the 8 children of each voxel; max pooling keeps the index
 // of the first maximum.
 namespace {
